@@ -1,0 +1,323 @@
+"""Benchmark of the GB300 dichotomy solver on the precision workload.
+
+Workload (one "step"): one solve of the series A X_n = F_n with n = 16384
+unknowns and N = 8192 right-hand sides, a_i = -1, b_i = 2 + s (s = 1e-6, the
+worst conditioning of the workload's range 10^[-6, 0], kappa ~ 3.9e6), F ~ N(0,1)
+in binary32, solved by the refined path (binary32 dichotomy solves + error-free
+residual refinement, binary64 output) to 1e-11 relative error.  The plain
+binary64 and binary32 dichotomy solves of the same series are measured beside
+it.  Inputs are resident in HBM and larger than L2 (F: 512 MiB, X: 1 GiB).
+
+Prints one JSON line (rank 0).  Multi-GPU (torchrun): every rank solves its own
+N-column series (weak scaling, no collective in the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_ROWS, N_RHS, SHIFT = 16384, 8192, 1e-6
+METRIC = "unknowns solved/s (n*N/s) and % of HBM roofline, FP32+refine vs FP64 at 1e-11 err"
+UNIT = "unknowns/s"
+WORKLOAD = "precision n=16384 N=8192 s=1e-6 (a=-1, b=2+s), F~N(0,1) fp32, refined to 1e-11"
+DIST = dict(rank=int(os.environ.get("RANK", 0)), world=int(os.environ.get("WORLD_SIZE", 1)),
+            local=int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0901_2859_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t.get(kernel)
+        if e and e.get("source_hash") == _kernel_hash():
+            return float(e["bytes_per_launch_full"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _events_time(fn, steps: int, warmup: int, torch):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    _barrier()
+    return e0.elapsed_time(e1) / steps   # ms per call, this rank
+
+
+def _barrier():
+    if DIST["world"] > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, torch) -> float:
+    if DIST["world"] <= 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=torch.device("cuda", DIST["local"]))
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _cpu_baseline(series, cols_target: int, X_gpu_cols=None):
+    """The oracle's binary64 sweep on a bounded sample of the workload's columns (host cores)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    k = max(1, min(series.N, cols_target))
+    Fs = np.ascontiguousarray(series.F[:, :k], dtype=np.float64)
+    oracle.thomas_f64(series.a, series.b, Fs[:, :min(k, 8)], threads=threads)   # warm-up
+    t0 = time.perf_counter()
+    oracle.thomas_f64(series.a, series.b, Fs, threads=threads)
+    dt = time.perf_counter() - t0
+    out = {"value": series.n * k / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"oracle binary64 sweep (thomas_f64) on the first {k} of {series.N} right-hand sides, "
+                     f"n={series.n}, {dt:.2f} s"}
+    if X_gpu_cols is not None:
+        idx, Xg = X_gpu_cols
+        ref = oracle.solve_hi(series.a, series.b, np.ascontiguousarray(series.F[:, idx], dtype=np.float64))
+        den = np.maximum(np.abs(ref).max(axis=0), 1e-300)
+        out["refined_rel_err_vs_oracle"] = float(np.max(np.abs(Xg - ref).max(axis=0) / den))
+        out["error_columns"] = len(idx)
+    return out
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import paper_0901_2859_gb300 as tdm
+    from paper_0901_2859_gb300 import workloads
+
+    if DIST["world"] > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", DIST["local"]))
+    dev = torch.device("cuda", DIST["local"])
+    torch.cuda.set_device(dev)
+    series = workloads.precision(seed=DIST["rank"], n=N_ROWS, N=N_RHS, s=SHIFT)
+    plan = tdm.prepare(series.a, series.b, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan2 = tdm.prepare(series.a, series.b, device=dev)
+    prepare_ms = (time.perf_counter() - t0) * 1e3
+    plan2.close()
+    info = plan.info()
+    F = torch.from_numpy(series.F).to(dev)
+    X = torch.empty((N_ROWS, N_RHS), dtype=torch.float64, device=dev)
+    unknowns = N_ROWS * N_RHS
+
+    # ---- headline: refined path --------------------------------------------------------
+    with ClockSampler(DIST["local"]) as clk:
+        ms = _events_time(lambda: plan.solve(F, "fp32_refined", out=X), args.steps, args.warmup, torch)
+    ms = _max_over_ranks(ms, torch)
+    value = DIST["world"] * unknowns / (ms * 1e-3)
+    hbm, peak_kind = _peaks()
+    bytes_refined = unknowns * (4 + 8)
+    achieved = bytes_refined / (ms * 1e-3) / 1e9
+    traffic = _traffic("k_solve_refined")
+
+    # ---- comparison paths: plain binary64 and plain binary32 dichotomy ------------------------
+    F64 = F.double()
+    X32 = torch.empty((N_ROWS, N_RHS), dtype=torch.float32, device=dev)
+    k64 = max(3, min(args.steps, 50))
+    ms64 = _max_over_ranks(_events_time(lambda: plan.solve(F64, "fp64", out=X), k64, 2, torch), torch)
+    ms32 = _max_over_ranks(_events_time(lambda: plan.solve(F, "fp32", out=X32), args.steps, args.warmup, torch), torch)
+    del F64
+
+    # ---- end to end: pinned host buffers, copies inside the timed region ----------------------
+    Fh = torch.from_numpy(series.F).pin_memory()
+    Xh = torch.empty((N_ROWS, N_RHS), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        F.copy_(Fh, non_blocking=True)
+        plan.solve(F, "fp32_refined", out=X)
+        Xh.copy_(X, non_blocking=True)
+
+    ke = max(3, min(args.steps, 20))
+    ms_e2e = _max_over_ranks(_events_time(e2e_step, ke, 2, torch), torch)
+
+    # the refined solution of a few columns, for the accuracy check of the baseline leg
+    plan.solve(F, "fp32_refined", out=X)
+    idx = np.array([0, 1, 2, 3, N_RHS // 2, N_RHS - 1])
+    Xcols = X[:, idx].cpu().numpy()
+    dev_err = plan.info()["device_error"]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": DIST["world"], "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_ROWS, "N": N_RHS, "s": SHIFT, "precision": "fp32_refined",
+                   "output": "f64", "refine_steps": info["refine_steps"], "block_rows": info["block_rows"],
+                   "parallelism": f"rhs-sharded x{DIST['world']}" if DIST["world"] > 1 else "single GPU",
+                   "l2": "no flush: F (512 MiB) and X (1 GiB) exceed L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
+                     "kernel": "k_solve_refined", "algorithmic_bytes_per_launch": bytes_refined},
+        "e2e": {"value": DIST["world"] * unknowns / (ms_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": unknowns * 4, "d2h_bytes_per_step": unknowns * 8},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "paths": {
+            "fp32_refined": {"ms": ms, "unknowns_per_s": value, "hbm_frac": achieved / hbm},
+            "fp64": {"ms": ms64, "unknowns_per_s": DIST["world"] * unknowns / (ms64 * 1e-3),
+                     "hbm_frac": unknowns * 16 / (ms64 * 1e-3) / 1e9 / hbm},
+            "fp32": {"ms": ms32, "unknowns_per_s": DIST["world"] * unknowns / (ms32 * 1e-3),
+                     "hbm_frac": unknowns * 8 / (ms32 * 1e-3) / 1e9 / hbm},
+            "refined_over_fp64": ms64 / ms,
+        },
+        "prepare_ms": prepare_ms, "device_error": dev_err,
+    }
+    if DIST["rank"] == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(series, args.cpu_cols, (idx, Xcols))
+    plan.close()
+    if DIST["rank"] == 0:
+        print(json.dumps(line), flush=True)
+    if DIST["world"] > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle (the plain CPU implementation), timed on the host cores on a bounded sample."""
+    if DIST["rank"] != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_0901_2859_gb300 import workloads
+    oracle.build()
+    series = workloads.precision(seed=0, n=N_ROWS, N=N_RHS, s=SHIFT)
+    threads = oracle.max_threads()
+    probe = np.ascontiguousarray(series.F[:, :256], dtype=np.float64)
+    t0 = time.perf_counter()
+    oracle.thomas_f64(series.a, series.b, probe, threads=threads)
+    per_col = (time.perf_counter() - t0) / 256
+    budget = 90.0 / max(1, args.steps + args.warmup)          # seconds per step
+    k = int(max(16, min(N_RHS, budget / max(per_col, 1e-9))))
+    Fs = np.ascontiguousarray(series.F[:, :k], dtype=np.float64)
+    for _ in range(args.warmup):
+        oracle.thomas_f64(series.a, series.b, Fs, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.thomas_f64(series.a, series.b, Fs, threads=threads)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = N_ROWS * k / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": DIST["world"],
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_ROWS, "N": N_RHS, "s": SHIFT},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"oracle binary64 sweep (thomas_f64) on {k} of {N_RHS} right-hand sides per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-cols", type=int, default=2048, help="columns of the CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * tdm.h -- C ABI of the GB300 library for series of symmetric tridiagonal
+ * systems solved by the parallel dichotomy (parallel sweep) method of
+ * A. V. Terekhov, "Parallel dichotomy algorithm for solving tridiagonal SLAEs".
+ *
+ * Problem (Section 2, eq. main_eq3): A X_n = F_n, n = 1..N, one constant,
+ * symmetric, nondegenerate tridiagonal A with diagonal b_0..b_{n-1} and
+ * off-diagonal a_0..a_{n-2} (A[i][i+1] = A[i+1][i] = a_i).
+ *
+ * Method (Algorithms 3 and 4, Theorem 2, Lemma 1): the rows are cut into M
+ * blocks of `block_rows` rows; block j >= 1 starts with a separator row.
+ *   prepare  (Algorithm 3/4 step 1, once per matrix): inverse rows G_k at the
+ *            separators over the two adjacent blocks (eq. green_v, Lemma 2),
+ *            the homogeneous ratios Z^R_k(k'), Z^L_k(k') between neighbouring
+ *            separators (eq. z_vector), the blocks' local sweep coefficients
+ *            and their homogeneous solutions; all in binary64 on the GPU.
+ *   solve    (step 2, per right-hand side): block-local dot products beta with
+ *            the inverse rows (eq. beta_symn), separator values from Theorem 2
+ *            evaluated as two first-order recurrences in binary64, then the
+ *            block interiors from the local sweep plus a correction with the
+ *            two separator values (Lemma 1).
+ *
+ * Conventions for every entry point
+ *  - Pointers to matrix data (a, b, F, X, W, dF, da, db) are DEVICE pointers
+ *    owned by the caller; the library never frees or keeps them.
+ *  - Right-hand sides are row-major [n][ld] with the right-hand sides
+ *    contiguous: element (row i, rhs r) is at F[i*ld + r]  (a PyTorch tensor
+ *    of shape (n, N) with stride (ld, 1)).  ld >= N.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Solves are asynchronous: a return of TDM_OK means the work was
+ *    validated and enqueued; device-side conditions are reported through
+ *    tdm_get_info, which synchronizes on the plan's last solve.
+ *  - Invalid arguments are rejected on the host before any launch with
+ *    TDM_ERR_INVALID_ARG; nothing is enqueued in that case.
+ *  - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef TDM_H
+#define TDM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdm_plan_s* tdm_handle;
+
+typedef enum {
+  TDM_OK = 0,
+  TDM_ERR_INVALID_ARG = 1,      /* bad size, stride, pointer alignment, aliasing, null handle */
+  TDM_ERR_SINGULAR = 2,         /* a binary64 pivot or an inverse-row diagonal vanished */
+  TDM_ERR_CUDA = 3,             /* a CUDA call or kernel launch failed */
+  TDM_ERR_NO_MEMORY = 4,        /* device allocation failed */
+  TDM_ERR_NOT_CONVERGED = 5,    /* refinement did not reach its tolerance within its cap */
+  TDM_ERR_TIMEOUT = 6,          /* a bounded device wait gave up */
+  TDM_ERR_NOT_IMPLEMENTED = 7   /* the requested combination is not available */
+} tdm_status;
+
+/* Arithmetic of a solve and the dtypes of F and X:
+ *   TDM_FP64          F, X binary64; sweeps and dot products in binary64.
+ *   TDM_FP32          F, X binary32; sweeps and dot products in binary32,
+ *                     separator recurrences in binary64.
+ *   TDM_FP32_REFINED  F binary32, X binary64; binary32 solves corrected by
+ *                     iterative refinement whose residual F - A X is formed
+ *                     with error-free binary32 transformations (at least
+ *                     binary64 accuracy), X accumulated as a binary32 pair. */
+typedef enum { TDM_FP64 = 0, TDM_FP32 = 1, TDM_FP32_REFINED = 2 } tdm_precision;
+
+typedef struct {
+  int block_rows;    /* rows per block (the paper's subvector size); 0 = automatic (32).
+                        Allowed: 16 or 32. */
+  int refine_steps;  /* TDM_FP32_REFINED corrections: k in 1..4 runs exactly k; 0 (automatic)
+                        stops once the estimated relative error is below 1e-12: max|d_1|/max|x|
+                        after the first correction, max|d_k|^2 / (max|x| max|d_{k-1}|) after
+                        later ones; at most 4 corrections (device_error 2 otherwise) */
+  int flags;         /* reserved, must be 0 */
+  int reserved;
+} tdm_options;
+
+typedef struct {
+  int64_t n;               /* system size */
+  int32_t block_rows;      /* rows per block */
+  int32_t num_blocks;      /* M = ceil(n / block_rows); separators = M - 1 */
+  int32_t dominant;        /* 1 if |b_i| >= |a_{i-1}| + |a_i| for all i with one strict
+                              inequality (Theorem 4: the method is then stable) */
+  int32_t refine_steps;    /* corrections of a TDM_FP32_REFINED solve; 0 = adaptive (at most 4) */
+  double max_abs_z;        /* max |Z^R|, |Z^L| ratio between neighbouring separators */
+  double min_abs_pivot;    /* smallest |pivot| met in prepare, relative to ||A||_inf */
+  int32_t device_error;    /* device-side error code of the last solves (0 = none,
+                              1 = a TMA transfer timed out, 2 = refinement cap reached
+                              before the convergence test passed) */
+  int32_t reserved;
+} tdm_info;
+
+/* tdm_prepare -- Algorithm 3/4, step 1 (Sections 3.3-3.4; eqs. green_v, z_vector).
+ *   a      device, n-1 binary64 off-diagonal entries (may be NULL when n == 1)
+ *   b      device, n binary64 diagonal entries
+ *   n      system size, 1 <= n <= 2^26
+ *   opt    may be NULL (all automatic)
+ *   stream enqueue the preparation on this stream; the call waits for it
+ *   out    receives the handle; the plan owns its device memory until
+ *          tdm_destroy.  a and b may be freed after the call returns.
+ * Errors: TDM_ERR_INVALID_ARG (n out of range, null pointers, 8-byte
+ * misalignment), TDM_ERR_SINGULAR (nondegeneracy violated, Section 2),
+ * TDM_ERR_NO_MEMORY, TDM_ERR_CUDA.  On error *out is set to NULL. */
+tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
+                       const tdm_options* opt, void* stream, tdm_handle* out);
+
+/* tdm_solve -- Algorithm 3/4, step 2 for every column (Theorem 2, Lemma 1).
+ *   F   device, [n][ldF], dtype per `prec` (binary64 for TDM_FP64, else binary32)
+ *   X   device, [n][ldX], binary64 for TDM_FP64 and TDM_FP32_REFINED, binary32
+ *       for TDM_FP32.  F and X must not overlap.
+ *   N   number of right-hand sides; N == 0 is a no-op.
+ * Pointers must be 16-byte aligned and ldF, ldX >= N.
+ * Errors: TDM_ERR_INVALID_ARG, TDM_ERR_CUDA. */
+tdm_status tdm_solve(tdm_handle h, const void* F, int64_t ldF, void* X, int64_t ldX,
+                     int64_t N, tdm_precision prec, void* stream);
+
+/* tdm_solve_batched -- many distinct constant matrices, each with its own
+ * block of right-hand sides (the per-mode series of the Fourier method,
+ * Section 4, eqs. series_fft, poisson_end), in one persistent launch.
+ *   hs[k], F[k], ldF[k], X[k], ldX[k], N[k] for k = 0..count-1, with the same
+ *   meaning as for tdm_solve (host arrays of device pointers).  All plans must
+ *   have the same block_rows.  The launch captures cleanly in a CUDA graph.
+ * Errors: as tdm_solve, plus TDM_ERR_INVALID_ARG for mixed block_rows. */
+tdm_status tdm_solve_batched(const tdm_handle* hs, int count,
+                             const void* const* F, const int64_t* ldF,
+                             void* const* X, const int64_t* ldX, const int64_t* N,
+                             tdm_precision prec, void* stream);
+
+/* tdm_solve_backward -- gradients of a scalar loss L through X = A^{-1} F.
+ * A is symmetric, so the adjoint system A^T Lambda = W is another solve with
+ * the same plan (Lemma 2).  With W = dL/dX and X the forward solution:
+ *   dF = Lambda,  db_i = -sum_r Lambda_ir X_ir,
+ *   da_i = -sum_r (Lambda_ir X_{i+1,r} + Lambda_{i+1,r} X_ir).
+ *   W, X   device [n][ld], binary32 (TDM_FP32) or binary64 (TDM_FP64)
+ *   dF     device [n][ld], same dtype; receives Lambda
+ *   da, db device binary64 arrays of n-1 and n entries, or NULL to skip
+ * The row sums over right-hand sides are accumulated in binary64 in a fixed
+ * order (deterministic).
+ * Errors: TDM_ERR_INVALID_ARG, TDM_ERR_NOT_IMPLEMENTED (TDM_FP32_REFINED), TDM_ERR_CUDA. */
+tdm_status tdm_solve_backward(tdm_handle h, const void* W, const void* X, int64_t ld,
+                              int64_t N, void* dF, double* da, double* db,
+                              tdm_precision prec, void* stream);
+
+/* tdm_get_info -- plan properties and the device status of the last solve
+ * (synchronizes with it). */
+tdm_status tdm_get_info(tdm_handle h, tdm_info* info);
+
+/* tdm_destroy -- releases the plan's device memory (synchronizes first).
+ * NULL is accepted and ignored. */
+tdm_status tdm_destroy(tdm_handle h);
+
+/* tdm_status_string -- static, human-readable name of a status code. */
+const char* tdm_status_string(tdm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDM_H */

@@ -1,0 +1,204 @@
+// tdm_api.cu -- the C ABI of include/tdm.h: argument validation, dispatch to
+// the solve kernels, the backward row sums, batched solves, plan info.
+#include <stdint.h>
+#include <string.h>
+
+#include "tdm_internal.cuh"
+
+tdm_status tdm_launch_plain(tdm_plan_s* p, const void* F, int64_t ldF, void* X, int64_t ldX,
+                            int64_t N, bool fp64, cudaStream_t s);
+tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX,
+                              int64_t N, cudaStream_t s);
+
+namespace {
+
+size_t elem_in(tdm_precision prec) { return prec == TDM_FP64 ? 8 : 4; }
+size_t elem_out(tdm_precision prec) { return prec == TDM_FP32 ? 4 : 8; }
+
+bool overlaps(const void* p0, size_t bytes0, const void* p1, size_t bytes1) {
+  const uintptr_t a0 = (uintptr_t)p0, a1 = (uintptr_t)p1;
+  return a0 < a1 + bytes1 && a1 < a0 + bytes0;
+}
+
+tdm_status validate_solve(const tdm_plan_s* h, const void* F, int64_t ldF, const void* X,
+                          int64_t ldX, int64_t N, tdm_precision prec) {
+  if (!h) return TDM_ERR_INVALID_ARG;
+  if (prec != TDM_FP64 && prec != TDM_FP32 && prec != TDM_FP32_REFINED) return TDM_ERR_INVALID_ARG;
+  if (N < 0 || N > (int64_t(1) << 40)) return TDM_ERR_INVALID_ARG;
+  if (N == 0) return TDM_OK;
+  if (!F || !X || ldF < N || ldX < N) return TDM_ERR_INVALID_ARG;
+  if (!tdm_aligned(F, 16) || !tdm_aligned(X, 16)) return TDM_ERR_INVALID_ARG;
+  const size_t bf = ((size_t)(h->n - 1) * (size_t)ldF + (size_t)N) * elem_in(prec);
+  const size_t bx = ((size_t)(h->n - 1) * (size_t)ldX + (size_t)N) * elem_out(prec);
+  if (overlaps(F, bf, X, bx)) return TDM_ERR_INVALID_ARG;
+  return TDM_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+// Backward row sums, deterministic: one CTA per row, each thread sums a fixed
+// strided subset of right-hand sides in order, then a fixed-shape tree.
+template <typename T>
+__global__ void __launch_bounds__(256) k_grad_rows(const T* __restrict__ L, const T* __restrict__ X,
+                                                   int64_t ld, int64_t N, int64_t n,
+                                                   double* __restrict__ da, double* __restrict__ db) {
+  __shared__ double sa[256], sb[256];
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    double accb = 0.0, acca = 0.0;
+    const bool has_next = i + 1 < n;
+    for (int64_t r = threadIdx.x; r < N; r += blockDim.x) {
+      const double li = (double)L[i * ld + r], xi = (double)X[i * ld + r];
+      accb = fma(li, xi, accb);
+      if (has_next) {
+        const double ln = (double)L[(i + 1) * ld + r], xn = (double)X[(i + 1) * ld + r];
+        acca = fma(li, xn, acca);
+        acca = fma(ln, xi, acca);
+      }
+    }
+    sa[threadIdx.x] = acca;
+    sb[threadIdx.x] = accb;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) {
+        sa[threadIdx.x] += sa[threadIdx.x + w];
+        sb[threadIdx.x] += sb[threadIdx.x + w];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      if (db) db[i] = -sb[0];
+      if (da && has_next) da[i] = -sa[0];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+tdm_status tdm_launch_solve(tdm_plan_s* p, const void* F, int64_t ldF, void* X, int64_t ldX,
+                            int64_t N, tdm_precision prec, cudaStream_t s) {
+  switch (prec) {
+    case TDM_FP64: return tdm_launch_plain(p, F, ldF, X, ldX, N, true, s);
+    case TDM_FP32: return tdm_launch_plain(p, F, ldF, X, ldX, N, false, s);
+    case TDM_FP32_REFINED:
+      return tdm_launch_refined(p, static_cast<const float*>(F), ldF, static_cast<double*>(X), ldX, N, s);
+  }
+  return TDM_ERR_INVALID_ARG;
+}
+
+tdm_status tdm_launch_backward_sums(tdm_plan_s* p, const void* W, const void* X, int64_t ld,
+                                    int64_t N, double* da, double* db, tdm_precision prec,
+                                    cudaStream_t s) {
+  (void)W;
+  if (!da && !db) return TDM_OK;
+  const int64_t n = p->n;
+  int grid = n < 65536 ? (int)n : 65536;
+  if (prec == TDM_FP64)
+    k_grad_rows<double><<<grid, 256, 0, s>>>(static_cast<const double*>(W), static_cast<const double*>(X),
+                                             ld, N, n, da, db);
+  else
+    k_grad_rows<float><<<grid, 256, 0, s>>>(static_cast<const float*>(W), static_cast<const float*>(X),
+                                            ld, N, n, da, db);
+  TDM_CUDA_TRY(cudaGetLastError());
+  return TDM_OK;
+}
+
+extern "C" tdm_status tdm_solve(tdm_handle h, const void* F, int64_t ldF, void* X, int64_t ldX,
+                                int64_t N, tdm_precision prec, void* stream) {
+  tdm_status st = validate_solve(h, F, ldF, X, ldX, N, prec);
+  if (st != TDM_OK || N == 0) return st;
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  st = tdm_launch_solve(h, F, ldF, X, ldX, N, prec, s);
+  if (st != TDM_OK) return st;
+  TDM_CUDA_TRY(cudaEventRecord(h->last, s));
+  return TDM_OK;
+}
+
+extern "C" tdm_status tdm_solve_batched(const tdm_handle* hs, int count, const void* const* F,
+                                        const int64_t* ldF, void* const* X, const int64_t* ldX,
+                                        const int64_t* N, tdm_precision prec, void* stream) {
+  if (count < 0 || (count > 0 && (!hs || !F || !ldF || !X || !ldX || !N))) return TDM_ERR_INVALID_ARG;
+  if (count == 0) return TDM_OK;
+  for (int k = 0; k < count; k++) {
+    tdm_status st = validate_solve(hs[k], F[k], ldF[k], X[k], ldX[k], N[k], prec);
+    if (st != TDM_OK) return st;
+    if (hs[k]->device != hs[0]->device || hs[k]->t != hs[0]->t) return TDM_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(hs[0]->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  tdm_status st = tdm_launch_batched(const_cast<tdm_plan_s* const*>(hs), count, F, ldF, X, ldX, N, prec, s);
+  if (st != TDM_OK) return st;
+  for (int k = 0; k < count; k++) TDM_CUDA_TRY(cudaEventRecord(hs[k]->last, s));
+  return TDM_OK;
+}
+
+extern "C" tdm_status tdm_solve_backward(tdm_handle h, const void* W, const void* X, int64_t ld,
+                                         int64_t N, void* dF, double* da, double* db,
+                                         tdm_precision prec, void* stream) {
+  if (!h) return TDM_ERR_INVALID_ARG;
+  if (prec == TDM_FP32_REFINED) return TDM_ERR_NOT_IMPLEMENTED;
+  if (prec != TDM_FP64 && prec != TDM_FP32) return TDM_ERR_INVALID_ARG;
+  if (N < 0 || ld < N) return TDM_ERR_INVALID_ARG;
+  if (N == 0) {
+    DeviceGuard g(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (da && h->n > 1) TDM_CUDA_TRY(cudaMemsetAsync(da, 0, sizeof(double) * (h->n - 1), s));
+    if (db) TDM_CUDA_TRY(cudaMemsetAsync(db, 0, sizeof(double) * h->n, s));
+    return TDM_OK;
+  }
+  if (!W || !X || !dF) return TDM_ERR_INVALID_ARG;
+  if (!tdm_aligned(X, 16) || (da && !tdm_aligned(da, 8)) || (db && !tdm_aligned(db, 8)))
+    return TDM_ERR_INVALID_ARG;
+  tdm_status st = validate_solve(h, W, ld, dF, ld, N, prec);
+  if (st != TDM_OK) return st;
+  const size_t bytes = ((size_t)(h->n - 1) * (size_t)ld + (size_t)N) * elem_in(prec);
+  if (overlaps(X, bytes, dF, bytes)) return TDM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  st = tdm_launch_solve(h, W, ld, dF, ld, N, prec, s);   // Lambda = A^{-1} W (A = A^T)
+  if (st != TDM_OK) return st;
+  st = tdm_launch_backward_sums(h, dF, X, ld, N, da, db, prec, s);
+  if (st != TDM_OK) return st;
+  TDM_CUDA_TRY(cudaEventRecord(h->last, s));
+  return TDM_OK;
+}
+
+extern "C" tdm_status tdm_get_info(tdm_handle h, tdm_info* info) {
+  if (!h || !info) return TDM_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  TDM_CUDA_TRY(cudaEventSynchronize(h->last));
+  int err = 0;
+  TDM_CUDA_TRY(cudaMemcpy(&err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  memset(info, 0, sizeof(*info));
+  info->n = h->n;
+  info->block_rows = h->t;
+  info->num_blocks = h->M;
+  info->dominant = h->dominant;
+  info->refine_steps = h->refine_steps;
+  info->max_abs_z = h->max_abs_z;
+  info->min_abs_pivot = h->min_abs_pivot;
+  info->device_error = err;
+  return TDM_OK;
+}
+
+extern "C" const char* tdm_status_string(tdm_status s) {
+  switch (s) {
+    case TDM_OK: return "TDM_OK";
+    case TDM_ERR_INVALID_ARG: return "TDM_ERR_INVALID_ARG";
+    case TDM_ERR_SINGULAR: return "TDM_ERR_SINGULAR";
+    case TDM_ERR_CUDA: return "TDM_ERR_CUDA";
+    case TDM_ERR_NO_MEMORY: return "TDM_ERR_NO_MEMORY";
+    case TDM_ERR_NOT_CONVERGED: return "TDM_ERR_NOT_CONVERGED";
+    case TDM_ERR_TIMEOUT: return "TDM_ERR_TIMEOUT";
+    case TDM_ERR_NOT_IMPLEMENTED: return "TDM_ERR_NOT_IMPLEMENTED";
+  }
+  return "TDM_ERR_UNKNOWN";
+}

@@ -1,0 +1,235 @@
+// tdm_kernel_common.cuh -- device pieces shared by the plain and the refined
+// solve kernels: cluster primitives, the shared-memory layout, and step A4
+// (separator values by Theorem 2, eq. theor_2) for one tile.
+#pragma once
+
+#include <stdint.h>
+
+#include "tdm_internal.cuh"
+
+namespace tdmk {
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// load a double from the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ double ld_cluster_f64(const double* local, unsigned rank) {
+  const unsigned laddr = (unsigned)__cvta_generic_to_shared(local);
+  unsigned raddr;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(laddr), "r"(rank));
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(raddr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ float ld_cluster_f32(const float* local, unsigned rank) {
+  const unsigned laddr = (unsigned)__cvta_generic_to_shared(local);
+  unsigned raddr;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(laddr), "r"(rank));
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(raddr) : "memory");
+  return v;
+}
+
+struct SolveArgs {
+  const void* F;
+  void* X;
+  int64_t ldF, ldX, N;
+  const void* coef;
+  const double* rR;
+  const double* rL;
+  int* err;
+  int n, M, m, C, ntiles;
+  int box_rows;   // TMA box height (divides m * t)
+};
+
+struct Smem {
+  double* lr;      // [(m+1) R]  local SR partials LR
+  double* ll;      // [(m+1) R]  local SL partials LL
+  double* piR;     // [m+1]
+  double* piL;     // [m+1]
+  double* rRloc;   // [m+1]
+  double* rLloc;   // [m+1]
+  double* piRtot;  // [16]
+  double* piLtot;  // [16]
+  double* xch;     // [2 parity][2 dir][R]  read by the other CTAs
+  double* in;      // [2][R]  incoming partials (binary64)
+  float* piR32;    // [m+1]
+  float* piL32;    // [m+1]
+  float* in32;     // [2][R]
+  void* betaR;     // [m R] T
+  void* betaL;     // [m R] T
+};
+
+__host__ __device__ inline size_t fbuf_bytes(int m, int t, int R, int tsize, bool tma) {
+  return tma ? (size_t)m * t * R * tsize : 0;
+}
+__host__ __device__ inline size_t coef_bytes(int m, int t, int tsize) {
+  return (size_t)m * t * kNCOEF * tsize;
+}
+__host__ __device__ inline size_t smem_bytes(int m, int t, int R, int tsize, bool tma) {
+  const size_t d = sizeof(double) * ((size_t)2 * (m + 1) * R + 4 * (m + 1) + 32 + 6 * R);
+  const size_t f = sizeof(float) * ((size_t)2 * (m + 1) + 2 * R);
+  const size_t tb = (size_t)tsize * 2 * m * R;
+  return 128 + fbuf_bytes(m, t, R, tsize, tma) + coef_bytes(m, t, tsize) + d + f + tb + 32;
+}
+
+// the 4 coefficients starting at p (16-byte aligned) in one or two vector loads
+__device__ __forceinline__ void ld4(const float* p, float& x, float& y, float& z, float& w) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x = v.x; y = v.y; z = v.z; w = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double& x, double& y, double& z, double& w) {
+  const double2 v0 = *reinterpret_cast<const double2*>(p);
+  const double2 v1 = *reinterpret_cast<const double2*>(p + 2);
+  x = v0.x; y = v0.y; z = v1.x; w = v1.y;
+}
+
+__device__ inline Smem carve(unsigned char* p, int m, int R, int tsize) {
+  Smem s;
+  double* d = reinterpret_cast<double*>(p);
+  s.lr = d; d += (m + 1) * R;
+  s.ll = d; d += (m + 1) * R;
+  s.piR = d; d += m + 1;
+  s.piL = d; d += m + 1;
+  s.rRloc = d; d += m + 1;
+  s.rLloc = d; d += m + 1;
+  s.piRtot = d; d += 16;
+  s.piLtot = d; d += 16;
+  s.xch = d; d += 4 * R;
+  s.in = d; d += 2 * R;
+  float* f = reinterpret_cast<float*>(d);
+  s.piR32 = f; f += m + 1;
+  s.piL32 = f; f += m + 1;
+  s.in32 = f; f += 2 * R;
+  unsigned char* q = reinterpret_cast<unsigned char*>(f);
+  q = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(q) + 15) & ~uintptr_t(15));
+  s.betaR = q; q += (size_t)tsize * m * R;
+  s.betaL = q;
+  return s;
+}
+
+// Ratios, prefix products within this CTA, and the per-CTA products of every
+// CTA of the cluster (used to fold the incoming partials).
+__device__ inline void setup_ratios(const SolveArgs& a, const Smem& s, unsigned c) {
+  const int m = a.m, M = a.M, b0 = (int)c * m;
+  auto rR = [&](int q) -> double { return (q >= 0 && q <= M + 1) ? a.rR[q] : 0.0; };
+  auto rL = [&](int q) -> double { return (q >= 0 && q <= M + 1) ? a.rL[q] : 0.0; };
+  const int tid = threadIdx.x;
+  for (int j = tid; j <= m; j += blockDim.x) {
+    s.rRloc[j] = (j >= 1) ? rR(b0 + j - 1) : 0.0;
+    s.rLloc[j] = (j < m) ? rL(b0 + j + 1) : 0.0;
+  }
+  if (tid == 0) {
+    double p = 1.0;
+    s.piR[0] = 1.0;
+    s.piR32[0] = 1.0f;
+    for (int j = 1; j <= m; j++) { p *= rR(b0 + j - 1); s.piR[j] = p; s.piR32[j] = (float)p; }
+  } else if (tid == 32) {
+    double p = 1.0;
+    s.piL[m] = 1.0;
+    s.piL32[m] = 1.0f;
+    for (int j = m - 1; j >= 0; j--) { p *= rL(b0 + j + 1); s.piL[j] = p; s.piL32[j] = (float)p; }
+  } else if (tid >= 64 && tid < 64 + a.C) {
+    const int cc = tid - 64, bb = cc * m;
+    double pr = 1.0, pl = 1.0;
+    for (int j = 1; j <= m; j++) pr *= rR(bb + j - 1);
+    for (int j = m - 1; j >= 0; j--) pl *= rL(bb + j + 1);
+    s.piRtot[cc] = pr;
+    s.piLtot[cc] = pl;
+  }
+}
+
+// A4 up to the incoming partials: LR/LL recurrences, exchange, folds.
+template <typename T, int R>
+__device__ __forceinline__ void separator_partials(const SolveArgs& a, const Smem& s, unsigned c, int parity) {
+  const int m = a.m;
+  const int tid = threadIdx.x;
+  const T* betaR = reinterpret_cast<const T*>(s.betaR);
+  const T* betaL = reinterpret_cast<const T*>(s.betaL);
+  double* xch = s.xch + parity * 2 * R;
+  if (tid < R) {                       // SR, left to right
+    const int r = tid;
+    double lr = 0.0;
+    s.lr[r] = 0.0;
+    for (int j = 1; j <= m; j++) {
+      lr = fma(s.rRloc[j], lr, tdm_to_f64<T>(betaR[(j - 1) * R + r]));
+      s.lr[j * R + r] = lr;
+    }
+    xch[r] = lr;
+  } else if (tid >= 32 && tid < 32 + R) {   // SL, right to left
+    const int r = tid - 32;
+    double ll = 0.0;
+    s.ll[m * R + r] = 0.0;
+    for (int j = m - 1; j >= 0; j--) {
+      ll = fma(s.rLloc[j], ll, tdm_to_f64<T>(betaL[j * R + r]));
+      s.ll[j * R + r] = ll;
+    }
+    xch[R + r] = ll;
+  }
+  cluster_barrier();
+  // fold the partials of the CTAs to the left (SR) and to the right (SL);
+  // remote loads are issued four at a time so that their latencies overlap
+  if (tid < R) {
+    const int r = tid;
+    double in = 0.0;
+    for (int c0 = 0; c0 < (int)c; c0 += 4) {
+      double v[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) v[k] = (c0 + k < (int)c) ? ld_cluster_f64(xch + r, (unsigned)(c0 + k)) : 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (c0 + k < (int)c) in = fma(s.piRtot[c0 + k], in, v[k]);
+    }
+    s.in[r] = in;
+    s.in32[r] = tdm_d2f(in);
+  } else if (tid >= 32 && tid < 32 + R) {
+    const int r = tid - 32;
+    double in = 0.0;
+    for (int c0 = a.C - 1; c0 > (int)c; c0 -= 4) {
+      double v[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) v[k] = (c0 - k > (int)c) ? ld_cluster_f64(xch + R + r, (unsigned)(c0 - k)) : 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (c0 - k > (int)c) in = fma(s.piLtot[c0 - k], in, v[k]);
+    }
+    s.in[R + r] = in;
+    s.in32[R + r] = tdm_d2f(in);
+  }
+  __syncthreads();
+}
+
+// x(p_{b0+j}) for rhs r, in the solve's type
+template <typename T, int R>
+__device__ __forceinline__ T separator_value(const Smem& s, int j, int r);
+template <>
+__device__ __forceinline__ double separator_value<double, 8>(const Smem& s, int j, int r) {
+  return fma(s.piR[j], s.in[r], fma(s.piL[j], s.in[8 + r], s.lr[j * 8 + r] + s.ll[j * 8 + r]));
+}
+template <>
+__device__ __forceinline__ double separator_value<double, 16>(const Smem& s, int j, int r) {
+  return fma(s.piR[j], s.in[r], fma(s.piL[j], s.in[16 + r], s.lr[j * 16 + r] + s.ll[j * 16 + r]));
+}
+template <>
+__device__ __forceinline__ double separator_value<double, 32>(const Smem& s, int j, int r) {
+  return fma(s.piR[j], s.in[r], fma(s.piL[j], s.in[32 + r], s.lr[j * 32 + r] + s.ll[j * 32 + r]));
+}
+template <int R>
+__device__ __forceinline__ float separator_value_f32(const Smem& s, int j, int r) {
+  const float loc = tdm_d2f(s.lr[j * R + r]) + tdm_d2f(s.ll[j * R + r]);
+  return fmaf(s.piR32[j], s.in32[r], fmaf(s.piL32[j], s.in32[R + r], loc));
+}
+template <>
+__device__ __forceinline__ float separator_value<float, 8>(const Smem& s, int j, int r) { return separator_value_f32<8>(s, j, r); }
+template <>
+__device__ __forceinline__ float separator_value<float, 16>(const Smem& s, int j, int r) { return separator_value_f32<16>(s, j, r); }
+template <>
+__device__ __forceinline__ float separator_value<float, 32>(const Smem& s, int j, int r) { return separator_value_f32<32>(s, j, r); }
+
+}  // namespace tdmk

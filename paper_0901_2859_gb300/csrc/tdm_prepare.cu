@@ -1,0 +1,351 @@
+// tdm_prepare.cu -- the preliminary step of Algorithms 3 and 4 (Sections 3.3-3.4),
+// executed once per matrix, in binary64, on the GPU.
+//
+// Rows are cut into blocks of t rows; block b covers [b*t, min(b*t+t, n)) and,
+// for b >= 1, starts with the separator row p_b = b*t.  The step computes
+//
+//  * the pivots of the sweep of A from the top (dF) and from the bottom (dB):
+//      dF_0 = b_0,      dF_i = b_i - a_{i-1}^2 / dF_{i-1},
+//      dB_{n-1} = b_{n-1}, dB_i = b_i - a_i^2 / dB_{i+1};
+//    their ratios -a_i/dF_i and -a_{i-1}/dB_i are the sweep coefficients of the
+//    homogeneous problems B^L_k Z = e^L and B^R_k Z = e^R of eq. z_vector
+//    (the alpha_i of the proof of Theorem 4);
+//  * for every separator k the inverse row G_k = A^{-1} e_k (eq. green_v;
+//    column = row by Lemma 2) on the two blocks next to it.  Its diagonal is
+//    G_k(k) = 1 / (dF_k - a_k^2 / dB_{k+1}), and away from k it follows the
+//    homogeneous solutions: G_k(i) = -a_i/dF_i * G_k(i+1) for i < k and
+//    G_k(i) = -a_{i-1}/dB_i * G_k(i-1) for i > k;
+//  * the ratios between neighbouring separators used by Theorem 2,
+//      rR_q = Z^R_{p_q}(p_{q+1}) = prod_{i=p_q+1}^{p_{q+1}} (-a_{i-1}/dB_i),
+//      rL_q = Z^L_{p_q}(p_{q-1}) = prod_{i=p_{q-1}}^{p_q - 1} (-a_i/dF_i);
+//  * for every block interior the local sweep (Lemma 1: the interior with both
+//    separator values known is an independent Dirichlet problem) and the
+//    interior's responses phiL, phiR to unit separator values;
+//  * checks: vanishing pivots (nondegeneracy, Section 2) and diagonal
+//    dominance (Theorem 4), plus the largest |rR|, |rL| and the smallest pivot.
+//
+// The pivots, the inverse rows and the ratios are carried in double-double
+// arithmetic and rounded to binary64 once.  In binary64 alone the pivot
+// recurrence and the cancellation in 1/(dF_k - a_k^2/dB_{k+1}) leave the
+// inverse rows of an ill-conditioned matrix (kappa ~ 1e6) only ~1e-12
+// accurate, and the separator values of Theorem 2 inherit that error
+// multiplied by sum |G_k(i) F_i| / |x_k|, which is large for oscillating F.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "tdm_dd.cuh"
+#include "tdm_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* slot, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_min_pos(unsigned long long* slot, double v) {
+  atomicMin(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+// stat[0]: flag bits; stat[1]: max |A| row sum; stat[2]: min |pivot|; stat[3]: max |z ratio|
+__global__ void k_norm_and_dominance(const double* __restrict__ a, const double* __restrict__ b,
+                                     int64_t n, unsigned long long* stat) {
+  double rmax = 0.0;
+  unsigned flags = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double al = (i > 0) ? fabs(a[i - 1]) : 0.0;
+    const double ar = (i + 1 < n) ? fabs(a[i]) : 0.0;
+    const double bi = fabs(b[i]);
+    if (!isfinite(bi) || !isfinite(al) || !isfinite(ar)) flags |= kStatNonFinite;
+    rmax = fmax(rmax, bi + al + ar);
+    if (bi < al + ar) flags |= kStatNotDominant;
+    if (bi > al + ar) flags |= kStatStrict;
+  }
+  if (flags) atomicOr(&stat[0], (unsigned long long)flags);
+  atomic_max_pos(&stat[1], rmax);
+}
+
+// Thread 0 sweeps from the top (dF), thread 1 from the bottom (dB), in double-double.
+__global__ void k_pivots(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                         dd* __restrict__ dF, dd* __restrict__ dB, unsigned long long* stat) {
+  const double normA = __longlong_as_double((long long)stat[1]);
+  const double tiny = 64.0 * 1.1102230246251565e-16 * normA;
+  double dmin = INFINITY;
+  if (threadIdx.x == 0) {
+    dd d = dd_make(b[0]);
+    dF[0] = d;
+    dmin = fabs(d.hi);
+    for (int64_t i = 1; i < n; i++) {
+      if (d.hi == 0.0) break;
+      d = dd_sub(dd_make(b[i]), dd_div(two_prod(a[i - 1], a[i - 1]), d));
+      dF[i] = d;
+      dmin = fmin(dmin, fabs(d.hi));
+    }
+  } else if (threadIdx.x == 1) {
+    dd d = dd_make(b[n - 1]);
+    dB[n - 1] = d;
+    dmin = fabs(d.hi);
+    for (int64_t i = n - 2; i >= 0; i--) {
+      if (d.hi == 0.0) break;
+      d = dd_sub(dd_make(b[i]), dd_div(two_prod(a[i], a[i]), d));
+      dB[i] = d;
+      dmin = fmin(dmin, fabs(d.hi));
+    }
+  } else {
+    return;
+  }
+  if (!(dmin > tiny) || !isfinite(dmin)) atomicOr(&stat[0], (unsigned long long)kStatSingular);
+  atomic_min_pos(&stat[2], isfinite(dmin) ? dmin : 0.0);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_row(T* dst, const double* v) {
+#pragma unroll
+  for (int k = 0; k < kNCOEF; k++) dst[k] = (T)v[k];
+}
+
+// One thread per block b.
+__global__ void k_block_coefficients(const double* __restrict__ a, const double* __restrict__ b,
+                                     int64_t n, int t, int M,
+                                     const dd* __restrict__ dF, const dd* __restrict__ dB,
+                                     double* __restrict__ coef64, float* __restrict__ coef32,
+                                     double* __restrict__ rR, double* __restrict__ rL,
+                                     unsigned long long* stat) {
+  const int bidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bidx >= M) return;
+  const double normA = __longlong_as_double((long long)stat[1]);
+  const double tiny = 64.0 * 1.1102230246251565e-16 * normA;
+  const int64_t lo = (int64_t)bidx * t;
+  const int64_t hi = (lo + t < n) ? lo + t : n;     // exclusive
+  const bool has_left = bidx >= 1;                  // separator at row lo
+  const bool has_right = hi < n;                    // separator at row hi
+  bool bad = false;
+  double zmax = 0.0;
+  double dmin = INFINITY;
+
+  // local arrays are small: t <= 64
+  double gR[64], gL[64], lf[64], invd[64], cc[64], phL[64], phR[64];
+  for (int i = 0; i < hi - lo; i++) {
+    gR[i] = gL[i] = lf[i] = invd[i] = cc[i] = phL[i] = phR[i] = 0.0;
+  }
+
+  // inverse-row diagonal at separator k: 1 / (dF_k - a_k^2 / dB_{k+1})
+  auto gdiag = [&](int64_t k) -> dd {
+    dd den = dF[k];
+    if (k + 1 < n) den = dd_sub(den, dd_div(two_prod(a[k], a[k]), dB[k + 1]));
+    if (!(fabs(den.hi) > 0.0) || !isfinite(den.hi)) { bad = true; return dd_make(0.0); }
+    return dd_div(dd_make(1.0), den);
+  };
+  auto ratio_up = [&](int64_t i) -> dd { return dd_div(dd_make(-a[i]), dF[i]); };        // G(i)/G(i+1), i < k
+  auto ratio_dn = [&](int64_t i) -> dd { return dd_div(dd_make(-a[i - 1]), dB[i]); };    // G(i)/G(i-1), i > k
+
+  if (has_right) {   // G_{hi}(i) for i = hi-1 .. lo
+    dd g = gdiag(hi);
+    for (int64_t i = hi - 1; i >= lo; i--) {
+      g = dd_mul(g, ratio_up(i));
+      gR[i - lo] = dd_to_d(g);
+    }
+  }
+  if (has_left) {    // G_{lo}(i) for i = lo .. hi-1
+    dd g = gdiag(lo);
+    gL[0] = dd_to_d(g);
+    for (int64_t i = lo + 1; i < hi; i++) {
+      g = dd_mul(g, ratio_dn(i));
+      gL[i - lo] = dd_to_d(g);
+    }
+  }
+  if (has_left && has_right) {
+    dd zr = dd_make(1.0), zl = dd_make(1.0);
+    for (int64_t i = lo + 1; i <= hi; i++) zr = dd_mul(zr, ratio_dn(i));
+    for (int64_t i = lo; i <= hi - 1; i++) zl = dd_mul(zl, ratio_up(i));
+    rR[bidx] = dd_to_d(zr);        // separator q = bidx (row lo) -> q+1 (row hi)
+    rL[bidx + 1] = dd_to_d(zl);    // separator q = bidx+1 (row hi) -> q-1 (row lo)
+    zmax = fmax(fabs(rR[bidx]), fabs(rL[bidx + 1]));
+  }
+
+  // local sweep of the interior [f, hi-1]
+  const int64_t f = has_left ? lo + 1 : lo;
+  const int64_t last = hi - 1;
+  if (f <= last) {
+    double d = b[f];
+    for (int64_t i = f; i <= last; i++) {
+      if (i > f) {
+        const double l = a[i - 1] / d;
+        lf[i - lo] = l;
+        d = b[i] - l * a[i - 1];
+      }
+      if (!(fabs(d) > tiny) || !isfinite(d)) bad = true;
+      dmin = fmin(dmin, fabs(d));
+      invd[i - lo] = 1.0 / d;
+      cc[i - lo] = (i < last) ? a[i] : 0.0;
+    }
+    if (has_left) {  // A_I phiL = -a_lo e_first
+      double g = -a[lo];
+      phL[f - lo] = g;   // forward values stored temporarily
+      for (int64_t i = f + 1; i <= last; i++) { g = -lf[i - lo] * g; phL[i - lo] = g; }
+      double y = 0.0;
+      for (int64_t i = last; i >= f; i--) { y = (phL[i - lo] - cc[i - lo] * y) * invd[i - lo]; phL[i - lo] = y; }
+    }
+    if (has_right) { // A_I phiR = -a_last e_last
+      double y = -a[last] * invd[last - lo];
+      phR[last - lo] = y;
+      for (int64_t i = last - 1; i >= f; i--) { y = -cc[i - lo] * y * invd[i - lo]; phR[i - lo] = y; }
+    }
+  }
+  if (has_left) {    // separator row: value comes from the separator recurrences
+    lf[0] = 0.0; invd[0] = 0.0; cc[0] = 0.0; phL[0] = 1.0; phR[0] = 0.0;
+  }
+
+  for (int64_t i = lo; i < hi; i++) {
+    const int k = (int)(i - lo);
+    double row[kNCOEF];
+    row[kGR] = gR[k]; row[kGL] = gL[k]; row[kLF] = lf[k]; row[3] = 0.0;
+    row[kC] = cc[k]; row[kINVD] = invd[k]; row[kPHIL] = phL[k]; row[kPHIR] = phR[k];
+    for (int c = 0; c < kNCOEF; c++)
+      if (!isfinite(row[c])) bad = true;
+    store_row(coef64 + i * kNCOEF, row);
+    store_row(coef32 + i * kNCOEF, row);
+  }
+  if (bad) atomicOr(&stat[0], (unsigned long long)kStatSingular);
+  if (isfinite(dmin)) atomic_min_pos(&stat[2], dmin);
+  atomic_max_pos(&stat[3], zmax);
+}
+
+// Residual coefficients: sigma_i = b_i + a_{i-1} + a_i formed exactly as a
+// double-double (two error-free sums), then sigma and a_i split into three
+// binary32 parts each.
+__device__ __forceinline__ void two_sum(double x, double y, double& s, double& e) {
+  s = x + y;
+  const double z = s - x;
+  e = (x - (s - z)) + (y - z);
+}
+__device__ __forceinline__ void split3(double hi, double lo, float* out) {
+  const float p0 = (float)hi;
+  const double r = (hi - (double)p0) + lo;
+  const float p1 = (float)r;
+  const float p2 = (float)(r - (double)p1);
+  out[0] = p0; out[1] = p1; out[2] = p2;
+}
+__global__ void k_residual_coefficients(const double* __restrict__ a, const double* __restrict__ b,
+                                        int64_t n, float* __restrict__ res32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double al = (i > 0) ? a[i - 1] : 0.0;
+    const double ar = (i + 1 < n) ? a[i] : 0.0;
+    double s1, e1, s2, e2;
+    two_sum(b[i], al, s1, e1);
+    two_sum(s1, ar, s2, e2);
+    double sh, sl;
+    two_sum(s2, e1 + e2, sh, sl);
+    float out[kNRES] = {0, 0, 0, 0, 0, 0, 0, 0};
+    split3(sh, sl, out + kS0);
+    split3(ar, 0.0, out + kA0);
+    for (int k = 0; k < kNRES; k++) res32[i * kNRES + k] = out[k];
+  }
+}
+
+}  // namespace
+
+static void tdm_free_plan(tdm_plan_s* p) {
+  if (!p) return;
+  cudaFree(p->coef64); cudaFree(p->coef32); cudaFree(p->res32);
+  cudaFree(p->rR); cudaFree(p->rL); cudaFree(p->a64); cudaFree(p->b64);
+  cudaFree(p->piv); cudaFree(p->stat); cudaFree(p->dev_err);
+  if (p->last) cudaEventDestroy(p->last);
+  delete p;
+}
+
+extern "C" tdm_status tdm_destroy(tdm_handle h) {
+  if (!h) return TDM_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  if (h->last) cudaEventSynchronize(h->last);
+  tdm_free_plan(h);
+  cudaSetDevice(cur);
+  return TDM_OK;
+}
+
+extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
+                                  const tdm_options* opt, void* stream, tdm_handle* out) {
+  if (!out) return TDM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || n > (int64_t(1) << 26) || !b || (n > 1 && !a)) return TDM_ERR_INVALID_ARG;
+  if (!tdm_aligned(b, 8) || (a && !tdm_aligned(a, 8))) return TDM_ERR_INVALID_ARG;
+  int t = 32, steps = 0;
+  if (opt) {
+    if (opt->flags != 0) return TDM_ERR_INVALID_ARG;
+    if (opt->block_rows != 0) t = opt->block_rows;
+    if (opt->refine_steps != 0) steps = opt->refine_steps;
+  }
+  if (t != 16 && t != 32) return TDM_ERR_INVALID_ARG;
+  if (steps < 0 || steps > 4) return TDM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  tdm_plan_s* p = new tdm_plan_s();
+  p->n = n;
+  p->t = t;
+  p->M = (int)((n + t - 1) / t);
+  p->refine_steps = steps;
+  cudaGetDevice(&p->device);
+  const int64_t na = n > 1 ? n - 1 : 1;
+  bool ok = cudaMalloc(&p->coef64, sizeof(double) * n * kNCOEF) == cudaSuccess &&
+            cudaMalloc(&p->coef32, sizeof(float) * n * kNCOEF) == cudaSuccess &&
+            cudaMalloc(&p->res32, sizeof(float) * n * kNRES) == cudaSuccess &&
+            cudaMalloc(&p->rR, sizeof(double) * (p->M + 2)) == cudaSuccess &&
+            cudaMalloc(&p->rL, sizeof(double) * (p->M + 2)) == cudaSuccess &&
+            cudaMalloc(&p->a64, sizeof(double) * na) == cudaSuccess &&
+            cudaMalloc(&p->b64, sizeof(double) * n) == cudaSuccess &&
+            cudaMalloc(&p->piv, sizeof(dd) * 2 * n) == cudaSuccess &&
+            cudaMalloc(&p->stat, sizeof(unsigned long long) * 8) == cudaSuccess &&
+            cudaMalloc(&p->dev_err, sizeof(int)) == cudaSuccess &&
+            cudaEventCreateWithFlags(&p->last, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    (void)cudaGetLastError();
+    tdm_free_plan(p);
+    return TDM_ERR_NO_MEMORY;
+  }
+  const double inf = INFINITY;
+  unsigned long long init[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  memcpy(&init[2], &inf, sizeof(double));
+  cudaError_t e = cudaSuccess;
+  if (n > 1) e = cudaMemcpyAsync(p->a64, a, sizeof(double) * (n - 1), cudaMemcpyDeviceToDevice, s);
+  else e = cudaMemsetAsync(p->a64, 0, sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->b64, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->stat, init, sizeof(init), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->rR, 0, sizeof(double) * (p->M + 2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->rL, 0, sizeof(double) * (p->M + 2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->dev_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_norm_and_dominance<<<64, 256, 0, s>>>(p->a64, p->b64, n, p->stat);
+    k_pivots<<<1, 32, 0, s>>>(p->a64, p->b64, n, reinterpret_cast<dd*>(p->piv), reinterpret_cast<dd*>(p->piv) + n, p->stat);
+    k_block_coefficients<<<(p->M + 127) / 128, 128, 0, s>>>(
+        p->a64, p->b64, n, t, p->M, reinterpret_cast<dd*>(p->piv), reinterpret_cast<dd*>(p->piv) + n, p->coef64, p->coef32, p->rR, p->rL, p->stat);
+    k_residual_coefficients<<<(int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, s>>>(
+        p->a64, p->b64, n, p->res32);
+    e = cudaGetLastError();
+  }
+  unsigned long long host_stat[8];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_stat, p->stat, sizeof(host_stat), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    tdm_free_plan(p);
+    return TDM_ERR_CUDA;
+  }
+  const unsigned flags = (unsigned)host_stat[0];
+  double normA, dmin, zmax;
+  memcpy(&normA, &host_stat[1], sizeof(double));
+  memcpy(&dmin, &host_stat[2], sizeof(double));
+  memcpy(&zmax, &host_stat[3], sizeof(double));
+  p->max_abs_z = zmax;
+  p->min_abs_pivot = normA > 0 ? dmin / normA : 0.0;
+  p->dominant = (!(flags & kStatNotDominant) && (flags & kStatStrict)) ? 1 : 0;
+  if (flags & (kStatSingular | kStatNonFinite)) {
+    tdm_free_plan(p);
+    return TDM_ERR_SINGULAR;
+  }
+  *out = p;
+  return TDM_OK;
+}

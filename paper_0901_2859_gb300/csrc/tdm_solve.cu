@@ -1,0 +1,325 @@
+// tdm_solve.cu -- step 2 of Algorithms 3/4 (Sections 3.3-3.4): the per
+// right-hand-side solve, fused into one persistent kernel per precision.
+//
+// Work decomposition.  A thread-block cluster owns a tile of R right-hand
+// sides and ALL n rows; CTA c of the cluster owns m consecutive blocks of t
+// rows (the paper's PE owns one sub-vector, Section 2); thread (block bl,
+// rhs r) owns the t rows of one block for one right-hand side, so a warp's
+// lanes touch consecutive right-hand sides of the same row.
+//
+// Per tile:
+//  load  the CTA's rows of the tile arrive in shared memory by TMA (issued
+//        while the previous tile was being computed) and move to registers;
+//  A2    beta^R_b = sum_{i in block b} G_{p_{b+1}}(i) F_i,
+//        beta^L_b = sum_{i in block b} G_{p_b}(i) F_i            (eq. beta_symn)
+//  A3    forward elimination of the block interior's local sweep (Lemma 1),
+//        fused with A2 in one pass over the rows held in registers;
+//  A4    separator values by Theorem 2 (eq. theor_2).  With the ratios
+//        rR_q = Z^R_{p_q}(p_{q+1}) and rL_q = Z^L_{p_q}(p_{q-1}) the two sums of
+//        Theorem 2 obey first-order recurrences
+//            SR_q = beta^R_{q-1} + rR_{q-1} SR_{q-1},
+//            SL_q = beta^L_q     + rL_{q+1} SL_{q+1},    x(p_q) = SR_q + SL_q,
+//        because Z^R_{p_j}(p_i) = prod_{k=j}^{i-1} rR_k (a homogeneous solution
+//        restricted to [p_k, n) is a multiple of Z^R_{p_k}), and likewise for
+//        Z^L.  Each CTA runs both recurrences over its own blocks from zero in
+//        binary64 (LR, LL); the CTAs exchange one partial per direction through
+//        distributed shared memory; the incoming partials inR, inL enter as
+//        x(p_q) = LR_q + LL_q + piR_q inR + piL_q inL with prefix products
+//        piR, piL of the ratios.  This is the GPU form of the dichotomy's
+//        level-by-level schedule (Algorithm 4): depth O(m + C), O(M) work.
+//  A5    back substitution of the local sweep and the correction
+//        x_i = y_i + phiL_i x(p_b) + phiR_i x(p_{b+1}); one coalesced store.
+// F is read once and X written once per tile.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cudaTypedefs.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "tdm_internal.cuh"
+#include "tdm_tma.cuh"
+
+bool tdm_encode_tma_2d(CUtensorMap* out, const void* base, bool fp64, uint64_t cols, uint64_t rows,
+                       uint64_t ld_bytes, uint32_t box_cols, uint32_t box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      (void)cudaGetLastError();
+  });
+  const uint64_t es = fp64 ? 8 : 4;
+  if (!fn || (reinterpret_cast<uintptr_t>(base) % 16) || (ld_bytes % 16) || ((box_cols * es) % 16) ||
+      box_cols > 256 || box_rows > 256 || cols < box_cols || ld_bytes >= (1ull << 40))
+    return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld_bytes};
+  cuuint32_t box[2] = {box_cols, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(out, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+#include "tdm_kernel_common.cuh"
+
+namespace {
+using namespace tdmk;
+
+template <typename T, int R, int TT, int MAXT, bool TMA>
+__global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const __grid_constant__ CUtensorMap tmF, const SolveArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int wait_ok;
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  T* fbuf = reinterpret_cast<T*>(base);
+  T* scf = reinterpret_cast<T*>(base + fbuf_bytes(a.m, TT, R, (int)sizeof(T), TMA));   // [m*t][8]
+  const Smem s = carve(reinterpret_cast<unsigned char*>(scf) + coef_bytes(a.m, TT, (int)sizeof(T)), a.m, R,
+                       (int)sizeof(T));
+  const unsigned c = cluster_rank();
+  const int tid = threadIdx.x;
+  const int r = tid % R;
+  const int bl = tid / R;
+  const int b = (int)c * a.m + bl;
+  const bool blk_ok = (bl < a.m) && (b < a.M);
+  const int64_t row0 = (int64_t)b * TT;
+  // rows of this thread's block that exist (0 for padding threads)
+  const int nrows = blk_ok ? (int)((a.n - row0) < TT ? (a.n - row0) : TT) : 0;
+  const int rows_cta = a.m * TT;
+  const int64_t cta_row0 = (int64_t)c * rows_cta;
+  const T* __restrict__ F = static_cast<const T*>(a.F);
+  T* __restrict__ X = static_cast<T*>(a.X);
+  const T* __restrict__ coef = static_cast<const T*>(a.coef);
+  const int n = a.n;
+
+  setup_ratios(a, s, c);
+  {   // this CTA's coefficient rows stay in shared memory for every tile
+    const int nvec = rows_cta * kNCOEF / 4;
+    for (int k = tid; k < nvec; k += blockDim.x) {
+      const int64_t row = cta_row0 + (k * 4) / kNCOEF;
+      T x = T(0), y = T(0), z = T(0), w = T(0);
+      if (row < n) ld4(coef + cta_row0 * kNCOEF + (int64_t)k * 4, x, y, z, w);
+      T* d = scf + (size_t)k * 4;
+      d[0] = x; d[1] = y; d[2] = z; d[3] = w;
+    }
+  }
+  if (TMA && tid == 0) tdm_mbar_init(&mbar, 1);
+  __syncthreads();
+
+  const int cluster_id = blockIdx.x / a.C;
+  const int nclusters = gridDim.x / a.C;
+  const uint32_t tile_bytes = (uint32_t)rows_cta * R * sizeof(T);
+  const int nbox = rows_cta / a.box_rows;
+  auto issue = [&](int tile) {
+    tdm_mbar_expect_tx(&mbar, tile_bytes);
+    for (int k = 0; k < nbox; k++)
+      tdm_tma_load_2d(fbuf + (size_t)k * a.box_rows * R, &tmF, tile * R, (int)(cta_row0 + (int64_t)k * a.box_rows), &mbar);
+  };
+  if (TMA && tid == 0 && cluster_id < a.ntiles) issue(cluster_id);
+
+  uint32_t phase = 0;
+  bool abort = false;
+  int parity = 0;
+  for (int tile = cluster_id; tile < a.ntiles; tile += nclusters) {
+    const int64_t col = (int64_t)tile * R + r;
+    const bool col_ok = col < a.N;
+    T v[TT];
+    if constexpr (TMA) {
+      if (!abort && !tdm_mbar_wait_cta(&mbar, phase, a.err, &wait_ok)) abort = true;
+      phase ^= 1u;
+      const T* src = fbuf + (size_t)bl * TT * R + r;
+#pragma unroll
+      for (int i = 0; i < TT; i++) v[i] = blk_ok ? src[i * R] : T(0);
+      __syncthreads();
+      if (tid == 0 && !abort && tile + nclusters < a.ntiles) {
+        tdm_fence_proxy_async();
+        issue(tile + nclusters);
+      }
+    } else {
+      const T* Fp = F + row0 * a.ldF + col;
+#pragma unroll
+      for (int i = 0; i < TT; i++) v[i] = (i < nrows && col_ok) ? Fp[(int64_t)i * a.ldF] : T(0);
+    }
+    // A2 + A3 forward: one pass over the rows
+    T bR = T(0), bL = T(0), g = T(0);
+#pragma unroll
+    for (int i = 0; i < TT; i++) {
+      if (i < nrows) {
+        T gr, gl, lf, unused;
+        ld4(scf + (size_t)(bl * TT + i) * kNCOEF, gr, gl, lf, unused);
+        bR = fma(gr, v[i], bR);
+        bL = fma(gl, v[i], bL);
+        g = fma(-lf, g, v[i]);
+        v[i] = g;
+      }
+    }
+    if (bl < a.m) {
+      reinterpret_cast<T*>(s.betaR)[bl * R + r] = bR;
+      reinterpret_cast<T*>(s.betaL)[bl * R + r] = bL;
+    }
+    __syncthreads();
+    separator_partials<T, R>(a, s, c, parity);
+    // A5: back substitution + correction + store
+    T xL = T(0), xR = T(0);
+    if (blk_ok) {
+      if (b >= 1) xL = separator_value<T, R>(s, bl, r);
+      if (b + 1 <= a.M - 1) xR = separator_value<T, R>(s, bl + 1, r);
+    }
+    T y = T(0);
+    T* Xp = X + row0 * a.ldX + col;
+#pragma unroll
+    for (int i = TT - 1; i >= 0; i--) {
+      if (i < nrows) {
+        T cc, invd, phl, phr;
+        ld4(scf + (size_t)(bl * TT + i) * kNCOEF + 4, cc, invd, phl, phr);
+        y = fma(-cc, y, v[i]) * invd;
+        const T x = fma(phr, xR, fma(phl, xL, y));
+        if (col_ok) Xp[(int64_t)i * a.ldX] = x;
+      }
+    }
+    parity ^= 1;
+  }
+  // no CTA may leave while a peer can still read its shared memory
+  cluster_barrier();
+}
+
+// ---------------------------------------------------------------------------
+// launch configuration
+// ---------------------------------------------------------------------------
+struct Cfg {
+  int R = 0, m = 0, C = 0, threads = 0, box_rows = 0;
+  bool tma = false;
+  size_t smem = 0;
+};
+
+int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return v ? atoi(v) : dflt;
+}
+
+// binary32: 512 threads and at most ~111 KB of shared memory, so that two CTAs
+// (of different clusters) share an SM and one's exchange phase overlaps the
+// other's loads; binary64: 512 threads with 32 doubles per thread in registers.
+bool choose_cfg(int M, int t, bool fp64, Cfg& cfg) {
+  const int maxt = 512;
+  const int pref = env_int(fp64 ? "TDM_R_FP64" : "TDM_R_FP32", fp64 ? 16 : 32);
+  for (int R = pref; R >= 8; R /= 2) {
+    if (R != 8 && R != 16 && R != 32) continue;
+    const int m_max = maxt / R;
+    const int C = (M + m_max - 1) / m_max;
+    if (C > 16) continue;
+    const int m = (M + C - 1) / C;
+    int threads = ((m * R + 31) / 32) * 32;
+    if (threads < 96) threads = 96;
+    cfg.R = R; cfg.m = m; cfg.C = C; cfg.threads = threads;
+    int g = 1;
+    for (int d = 1; d <= m; d++)
+      if (m % d == 0 && d * t <= 256) g = d;
+    cfg.box_rows = g * t;
+    return true;
+  }
+  return false;
+}
+
+template <typename T, int R, int TT, int MAXT, bool TMA>
+tdm_status launch_t(const CUtensorMap& map, const SolveArgs& args, const Cfg& cfg, cudaStream_t s) {
+  auto kern = k_solve<T, R, TT, MAXT, TMA>;
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, size_t, int>, int> occ;  // (device, C, smem, threads) -> clusters
+  int dev = 0;
+  cudaGetDevice(&dev);
+  TDM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
+  if (cfg.C > 8) TDM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cfg.C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.blockDim = dim3(cfg.threads);
+  lc.dynamicSmemBytes = cfg.smem;
+  lc.stream = s;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  int maxc = 0;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_tuple(dev, cfg.C, cfg.smem, cfg.threads);
+    auto it = occ.find(key);
+    if (it != occ.end()) {
+      maxc = it->second;
+    } else {
+      lc.gridDim = dim3(cfg.C);
+      if (cudaOccupancyMaxActiveClusters(&maxc, (void*)kern, &lc) != cudaSuccess || maxc < 1) {
+        (void)cudaGetLastError();
+        maxc = 1;
+      }
+      occ[key] = maxc;
+    }
+  }
+  const int nclusters = args.ntiles < maxc ? args.ntiles : maxc;
+  lc.gridDim = dim3(nclusters * cfg.C);
+  TDM_CUDA_TRY(cudaLaunchKernelEx(&lc, kern, map, args));
+  return TDM_OK;
+}
+
+template <typename T, int TT, int MAXT>
+tdm_status dispatch(const CUtensorMap& map, const SolveArgs& args, const Cfg& cfg, cudaStream_t s) {
+  if (cfg.tma) {
+    switch (cfg.R) {
+      case 8: return launch_t<T, 8, TT, MAXT, true>(map, args, cfg, s);
+      case 16: return launch_t<T, 16, TT, MAXT, true>(map, args, cfg, s);
+      case 32: return launch_t<T, 32, TT, MAXT, true>(map, args, cfg, s);
+    }
+  } else {
+    switch (cfg.R) {
+      case 8: return launch_t<T, 8, TT, MAXT, false>(map, args, cfg, s);
+      case 16: return launch_t<T, 16, TT, MAXT, false>(map, args, cfg, s);
+      case 32: return launch_t<T, 32, TT, MAXT, false>(map, args, cfg, s);
+    }
+  }
+  return TDM_ERR_NOT_IMPLEMENTED;
+}
+
+}  // namespace
+
+tdm_status tdm_launch_plain(tdm_plan_s* p, const void* F, int64_t ldF, void* X, int64_t ldX,
+                            int64_t N, bool fp64, cudaStream_t s) {
+  Cfg cfg;
+  if (!choose_cfg(p->M, p->t, fp64, cfg)) return TDM_ERR_NOT_IMPLEMENTED;
+  const int tsize = fp64 ? 8 : 4;
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  cfg.tma = env_int("TDM_NO_TMA", 0) == 0 &&
+            tdm_encode_tma_2d(&map, F, fp64, (uint64_t)N, (uint64_t)p->n, (uint64_t)ldF * tsize,
+                              (uint32_t)cfg.R, (uint32_t)cfg.box_rows);
+  cfg.smem = smem_bytes(cfg.m, p->t, cfg.R, tsize, cfg.tma);
+  if (cfg.smem > 227 * 1024) {   // fall back to direct loads when the staging buffer does not fit
+    cfg.tma = false;
+    cfg.smem = smem_bytes(cfg.m, p->t, cfg.R, tsize, false);
+  }
+  SolveArgs args;
+  args.F = F; args.X = X; args.ldF = ldF; args.ldX = ldX; args.N = N;
+  args.coef = fp64 ? (const void*)p->coef64 : (const void*)p->coef32;
+  args.rR = p->rR; args.rL = p->rL; args.err = p->dev_err;
+  args.n = (int)p->n; args.M = p->M; args.m = cfg.m; args.C = cfg.C;
+  args.ntiles = (int)((N + cfg.R - 1) / cfg.R);
+  args.box_rows = cfg.box_rows;
+  if (fp64) {
+    if (p->t == 16) return dispatch<double, 16, 512>(map, args, cfg, s);
+    return dispatch<double, 32, 512>(map, args, cfg, s);
+  }
+  if (p->t == 16) return dispatch<float, 16, 512>(map, args, cfg, s);
+  return dispatch<float, 32, 512>(map, args, cfg, s);
+}

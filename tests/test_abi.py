@@ -1,0 +1,71 @@
+"""The C-ABI library loads, exports every symbol include/tdm.h declares, and
+rejects invalid arguments on the host (no GPU work is issued by these calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "tdm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tdm_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0901_2859_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_documented_entry_points():
+    from paper_0901_2859_gb300 import _lib
+    assert _declared_symbols() == sorted(_lib.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    from paper_0901_2859_gb300 import _lib
+    for code, name in _lib.STATUS_NAMES.items():
+        assert lib.tdm_status_string(code).decode() == name
+    assert lib.tdm_status_string(99).decode() == "TDM_ERR_UNKNOWN"
+
+
+def test_host_validation_rejects_bad_arguments(lib):
+    vp = ctypes.c_void_p
+    h = vp()
+    fake = vp(0x10000)
+    # tdm_prepare: null out, n < 1, null b, misaligned b
+    assert lib.tdm_prepare(fake, fake, 10, None, None, None) == 1
+    assert lib.tdm_prepare(fake, fake, 0, None, None, ctypes.byref(h)) == 1
+    assert h.value is None
+    assert lib.tdm_prepare(fake, None, 10, None, None, ctypes.byref(h)) == 1
+    assert lib.tdm_prepare(fake, vp(0x10004), 10, None, None, ctypes.byref(h)) == 1
+    # tdm_solve / backward / info with a null handle
+    assert lib.tdm_solve(None, fake, 4, vp(0x20000), 4, 4, 1, None) == 1
+    assert lib.tdm_solve_backward(None, fake, fake, 4, 4, fake, None, None, 1, None) == 1
+    assert lib.tdm_get_info(None, None) == 1
+    # batched: negative count, null arrays
+    assert lib.tdm_solve_batched(None, -1, None, None, None, None, None, 2, None) == 1
+    assert lib.tdm_solve_batched(None, 3, None, None, None, None, None, 2, None) == 1
+    assert lib.tdm_solve_batched(None, 0, None, None, None, None, None, 2, None) == 0
+    # destroy(NULL) is accepted
+    assert lib.tdm_destroy(None) == 0
+
+
+def test_bad_block_rows_rejected_before_any_cuda_call(lib):
+    from paper_0901_2859_gb300._lib import TDMOptions
+    h = ctypes.c_void_p()
+    opt = TDMOptions(24, 0, 0, 0)
+    assert lib.tdm_prepare(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), 100, ctypes.byref(opt),
+                           None, ctypes.byref(h)) == 1
+    opt = TDMOptions(32, 9, 0, 0)
+    assert lib.tdm_prepare(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), 100, ctypes.byref(opt),
+                           None, ctypes.byref(h)) == 1
