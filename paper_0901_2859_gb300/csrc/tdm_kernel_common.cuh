@@ -14,8 +14,14 @@ __device__ __forceinline__ unsigned cluster_rank() {
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
   return r;
 }
+// Cluster-wide barrier.  Every thread arrives (release); warp 0 alone waits
+// for the other CTAs while the remaining warps sleep in the CTA barrier, then
+// they complete their own wait (acquire) on the already finished phase.
 __device__ __forceinline__ void cluster_barrier() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  if (threadIdx.x < 32) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x >= 32) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 // load a double from the same shared-memory offset in CTA `rank` of the cluster
 __device__ __forceinline__ double ld_cluster_f64(const double* local, unsigned rank) {
@@ -62,8 +68,8 @@ struct Smem {
   float* piR32;    // [m+1]
   float* piL32;    // [m+1]
   float* in32;     // [2][R]
-  void* betaR;     // [m R] T
-  void* betaL;     // [m R] T
+  double* betaR;   // [m R] beta^R of every block, converted to binary64 by its thread
+  double* betaL;   // [m R]
 };
 
 __host__ __device__ inline size_t fbuf_bytes(int m, int t, int R, int tsize, bool tma) {
@@ -73,10 +79,12 @@ __host__ __device__ inline size_t coef_bytes(int m, int t, int tsize) {
   return (size_t)m * t * kNCOEF * tsize;
 }
 __host__ __device__ inline size_t smem_bytes(int m, int t, int R, int tsize, bool tma) {
-  const size_t d = sizeof(double) * ((size_t)2 * (m + 1) * R + 4 * (m + 1) + 32 + 6 * R);
-  const size_t f = sizeof(float) * ((size_t)2 * (m + 1) + 2 * R);
-  const size_t tb = (size_t)tsize * 2 * m * R;
-  return 128 + fbuf_bytes(m, t, R, tsize, tma) + coef_bytes(m, t, tsize) + d + f + tb + 32;
+  // interface arrays as laid out by carve(), each rounded up to 16 bytes
+  const size_t d = 2 * (sizeof(double) * (m + 1) * R + 16) + 4 * (sizeof(double) * (m + 1) + 16) + 256 +
+                   (sizeof(double) * 6 * R + 32);
+  const size_t f = 2 * (sizeof(float) * (m + 1) + 16) + sizeof(float) * 2 * R + 16;
+  const size_t tb = 2 * (sizeof(double) * m * R + 16);
+  return 128 + fbuf_bytes(m, t, R, tsize, tma) + coef_bytes(m, t, tsize) + d + f + tb;
 }
 
 // the 4 coefficients starting at p (16-byte aligned) in one or two vector loads
@@ -90,28 +98,35 @@ __device__ __forceinline__ void ld4(const double* p, double& x, double& y, doubl
   x = v0.x; y = v0.y; z = v1.x; w = v1.y;
 }
 
+__host__ __device__ constexpr size_t round16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Carves the interface arrays out of shared memory starting at p (16-byte
+// aligned).  Pointers are derived from the __shared__ array by pointer
+// arithmetic only, so the compiler keeps them in the shared address space.
 __device__ inline Smem carve(unsigned char* p, int m, int R, int tsize) {
   Smem s;
-  double* d = reinterpret_cast<double*>(p);
-  s.lr = d; d += (m + 1) * R;
-  s.ll = d; d += (m + 1) * R;
-  s.piR = d; d += m + 1;
-  s.piL = d; d += m + 1;
-  s.rRloc = d; d += m + 1;
-  s.rLloc = d; d += m + 1;
-  s.piRtot = d; d += 16;
-  s.piLtot = d; d += 16;
-  s.xch = d; d += 4 * R;
-  s.in = d; d += 2 * R;
-  float* f = reinterpret_cast<float*>(d);
-  s.piR32 = f; f += m + 1;
-  s.piL32 = f; f += m + 1;
-  s.in32 = f; f += 2 * R;
-  unsigned char* q = reinterpret_cast<unsigned char*>(f);
-  q = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(q) + 15) & ~uintptr_t(15));
-  s.betaR = q; q += (size_t)tsize * m * R;
-  s.betaL = q;
+  s.lr = reinterpret_cast<double*>(p); p += round16(sizeof(double) * (m + 1) * R);
+  s.ll = reinterpret_cast<double*>(p); p += round16(sizeof(double) * (m + 1) * R);
+  s.piR = reinterpret_cast<double*>(p); p += round16(sizeof(double) * (m + 1));
+  s.piL = reinterpret_cast<double*>(p); p += round16(sizeof(double) * (m + 1));
+  s.rRloc = reinterpret_cast<double*>(p); p += round16(sizeof(double) * (m + 1));
+  s.rLloc = reinterpret_cast<double*>(p); p += round16(sizeof(double) * (m + 1));
+  s.piRtot = reinterpret_cast<double*>(p); p += sizeof(double) * 16;
+  s.piLtot = reinterpret_cast<double*>(p); p += sizeof(double) * 16;
+  s.xch = reinterpret_cast<double*>(p); p += round16(sizeof(double) * 4 * R);
+  s.in = reinterpret_cast<double*>(p); p += round16(sizeof(double) * 2 * R);
+  s.piR32 = reinterpret_cast<float*>(p); p += round16(sizeof(float) * (m + 1));
+  s.piL32 = reinterpret_cast<float*>(p); p += round16(sizeof(float) * (m + 1));
+  s.in32 = reinterpret_cast<float*>(p); p += round16(sizeof(float) * 2 * R);
+  (void)tsize;
+  s.betaR = reinterpret_cast<double*>(p); p += round16(sizeof(double) * m * R);
+  s.betaL = reinterpret_cast<double*>(p);
   return s;
+}
+
+// byte offset that aligns the dynamic shared-memory window to 128 bytes
+__device__ __forceinline__ unsigned smem_align_pad(const void* smem_base) {
+  return (128u - ((unsigned)__cvta_generic_to_shared(smem_base) & 127u)) & 127u;
 }
 
 // Ratios, prefix products within this CTA, and the per-CTA products of every
@@ -150,15 +165,16 @@ template <typename T, int R>
 __device__ __forceinline__ void separator_partials(const SolveArgs& a, const Smem& s, unsigned c, int parity) {
   const int m = a.m;
   const int tid = threadIdx.x;
-  const T* betaR = reinterpret_cast<const T*>(s.betaR);
-  const T* betaL = reinterpret_cast<const T*>(s.betaL);
+  const double* betaR = s.betaR;
+  const double* betaL = s.betaL;
   double* xch = s.xch + parity * 2 * R;
   if (tid < R) {                       // SR, left to right
     const int r = tid;
     double lr = 0.0;
     s.lr[r] = 0.0;
-    for (int j = 1; j <= m; j++) {
-      lr = fma(s.rRloc[j], lr, tdm_to_f64<T>(betaR[(j - 1) * R + r]));
+#pragma unroll 2
+    for (int j = 1; j <= m; j++) {   // loads do not depend on the chain: only the fma is serial
+      lr = fma(s.rRloc[j], lr, betaR[(j - 1) * R + r]);
       s.lr[j * R + r] = lr;
     }
     xch[r] = lr;
@@ -166,8 +182,9 @@ __device__ __forceinline__ void separator_partials(const SolveArgs& a, const Sme
     const int r = tid - 32;
     double ll = 0.0;
     s.ll[m * R + r] = 0.0;
+#pragma unroll 2
     for (int j = m - 1; j >= 0; j--) {
-      ll = fma(s.rLloc[j], ll, tdm_to_f64<T>(betaL[j * R + r]));
+      ll = fma(s.rLloc[j], ll, betaL[j * R + r]);
       s.ll[j * R + r] = ll;
     }
     xch[R + r] = ll;
@@ -231,5 +248,46 @@ template <>
 __device__ __forceinline__ float separator_value<float, 16>(const Smem& s, int j, int r) { return separator_value_f32<16>(s, j, r); }
 template <>
 __device__ __forceinline__ float separator_value<float, 32>(const Smem& s, int j, int r) { return separator_value_f32<32>(s, j, r); }
+
+// A2 + A3 over one block held in v[] (overwritten with the forward-eliminated
+// values): the two beta dot products and the local sweep's forward pass.
+// FULL: all TT rows exist, so no per-row test is compiled in.
+template <typename T, int TT, bool FULL>
+__device__ __forceinline__ void forward_pass(T (&v)[TT], const T* cf, int nrows, T& bR, T& bL) {
+  T g = T(0);
+#pragma unroll
+  for (int i = 0; i < TT; i++) {
+    if (FULL || i < nrows) {
+      T gr, gl, lf, unused;
+      ld4(cf + i * kNCOEF, gr, gl, lf, unused);
+      bR = fma(gr, v[i], bR);
+      bL = fma(gl, v[i], bL);
+      g = fma(-lf, g, v[i]);
+      v[i] = g;
+    }
+  }
+}
+
+// A5 of the plain solve: back substitution, correction with the two separator
+// values, and the store of each row; p points at the block's first row of X.
+template <typename T, int TT, bool FULL>
+__device__ __forceinline__ void backward_store(const T (&v)[TT], const T* cf, int nrows, T xL, T xR, T* p,
+                                               int64_t ld, bool col_ok) {
+  T y = T(0);
+  const int last = FULL ? TT - 1 : nrows - 1;
+  if (!FULL && last < 0) return;
+  p += (int64_t)last * ld;
+#pragma unroll
+  for (int i = TT - 1; i >= 0; i--) {
+    if (FULL || i <= last) {
+      T cc, invd, phl, phr;
+      ld4(cf + i * kNCOEF + 4, cc, invd, phl, phr);
+      y = fma(-cc, y, v[i]) * invd;
+      const T x = fma(phr, xR, fma(phl, xL, y));
+      if (col_ok) *p = x;
+      p -= ld;
+    }
+  }
+}
 
 }  // namespace tdmk

@@ -80,16 +80,40 @@ __device__ __forceinline__ float cluster_ratio(const float* slot, int C, int tid
   return *bcast;
 }
 
+// A5 of a correction solve: back substitution, correction with the separator
+// values, and x += d in pair arithmetic (high words in registers, low words in
+// shared memory at stride R); tracks max|d| and max|x| for the convergence test.
+template <int R, int TT, bool FULL>
+__device__ __forceinline__ void backward_update(const float (&g)[TT], const float* cf, int nrows, float xL,
+                                                float xR, float (&xh)[TT], float* xlt, float& maxd,
+                                                float& maxx) {
+  float y = 0.f;
+#pragma unroll
+  for (int i = TT - 1; i >= 0; i--) {
+    if (FULL || i < nrows) {
+      float cc, invd, phl, phr;
+      ld4(cf + i * kNCOEF + 4, cc, invd, phl, phr);
+      y = fmaf(-cc, y, g[i]) * invd;
+      const float d = fmaf(phr, xR, fmaf(phl, xL, y));
+      const f2pair xn = df_add_f(f2pair{xh[i], xlt[i * R]}, d);
+      xh[i] = xn.h;
+      xlt[i * R] = xn.l;
+      maxd = fmaxf(maxd, fabsf(d));
+      maxx = fmaxf(maxx, fabsf(xn.h));
+    }
+  }
+}
+
 template <int R, int TT, bool TMA>
 __global__ void __launch_bounds__(512, 1) k_solve_refined(const __grid_constant__ CUtensorMap tmF, const RefineArgs ra) {
   const SolveArgs& a = ra.s;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ int wait_ok;
   __shared__ float ratio_s;
   const int m = a.m;
   const int rows_cta = m * TT;
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  unsigned char* base = smem_raw + smem_align_pad(smem_raw);
   float* fbuf = reinterpret_cast<float*>(base);                         // [rows_cta][R]  F tile
   float* sxl = fbuf + (size_t)rows_cta * R;                             // [rows_cta][R]  low words of x
   float* scf = sxl + (size_t)rows_cta * R;                              // [rows_cta][8]
@@ -110,6 +134,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_refined(const __grid_constant_
   const int b = (int)c * m + bl;
   const bool blk_ok = (bl < m) && (b < a.M);
   const int64_t row0 = (int64_t)b * TT;
+  const int nrows = blk_ok ? (int)((a.n - row0) < TT ? (a.n - row0) : TT) : 0;   // rows that exist
   const int64_t cta_row0 = (int64_t)c * rows_cta;
   const int n = a.n;
   const float* __restrict__ coef = static_cast<const float*>(a.coef);
@@ -182,7 +207,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_refined(const __grid_constant_
     for (int step = 0;; step++) {
       if (step == 0) {
 #pragma unroll
-        for (int i = 0; i < TT; i++) g[i] = blk_ok ? Ft[i * R] : 0.f;
+        for (int i = 0; i < TT; i++) g[i] = blk_ok ? Ft[i * R] : 0.f;   // zeros beyond n
       } else {
         // ---- residual r = F - A x of the current iterate ------------------------
         // (threads beyond the CTA's m blocks only take part in the barriers)
@@ -225,7 +250,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_refined(const __grid_constant_
           const f2pair xn = (i + 1 < TT) ? f2pair{xh[i + 1], xlt[(i + 1) * R]} : xp;
           const f2pair E = df_mul(f2pair{ah, al}, df_diff(xn, xi));
           const f2pair S = df_mul(f2pair{sh, sl}, xi);
-          const float Fi = blk_ok ? Ft[i * R] : 0.f;
+          const float Fi = Ft[i * R];   // bl < m here; rows beyond n hold zeros
           const f2pair w = two_sum_f(Ep.h, -E.h);
           const f2pair u = two_sum_f(Fi, w.h);
           const f2pair v = two_sum_f(u.h, -S.h);
@@ -238,22 +263,13 @@ __global__ void __launch_bounds__(512, 1) k_solve_refined(const __grid_constant_
       }
 
       // ---- binary32 dichotomy solve of g (A2-A5) ---------------------------------
-      float bR = 0.f, bL = 0.f, gg = 0.f;
-#pragma unroll
-      for (int i = 0; i < TT; i++) {
-        const int64_t row = row0 + i;
-        if (blk_ok && row < n) {
-          float gr, gl, lf, unused;
-          ld4(scf + (size_t)(bl * TT + i) * kNCOEF, gr, gl, lf, unused);
-          bR = fmaf(gr, g[i], bR);
-          bL = fmaf(gl, g[i], bL);
-          gg = fmaf(-lf, gg, g[i]);
-          g[i] = gg;
-        }
-      }
+      const float* cfb = scf + (size_t)bl * TT * kNCOEF;
+      float bR = 0.f, bL = 0.f;
+      if (nrows == TT) forward_pass<float, TT, true>(g, cfb, nrows, bR, bL);
+      else forward_pass<float, TT, false>(g, cfb, nrows, bR, bL);
       if (bl < m) {
-        reinterpret_cast<float*>(s.betaR)[bl * R + r] = bR;
-        reinterpret_cast<float*>(s.betaL)[bl * R + r] = bL;
+        s.betaR[bl * R + r] = tdm_f2d(bR);
+        s.betaL[bl * R + r] = tdm_f2d(bL);
       }
       __syncthreads();
       separator_partials<float, R>(a, s, c, parity);
@@ -263,22 +279,9 @@ __global__ void __launch_bounds__(512, 1) k_solve_refined(const __grid_constant_
         if (b >= 1) xL = separator_value<float, R>(s, bl, r);
         if (b + 1 <= a.M - 1) xR = separator_value<float, R>(s, bl + 1, r);
       }
-      float y = 0.f, maxd = 0.f, maxx = 0.f;
-#pragma unroll
-      for (int i = TT - 1; i >= 0; i--) {
-        const int64_t row = row0 + i;
-        if (blk_ok && row < n) {
-          float cc, invd, phl, phr;
-          ld4(scf + (size_t)(bl * TT + i) * kNCOEF + 4, cc, invd, phl, phr);
-          y = fmaf(-cc, y, g[i]) * invd;
-          const float d = fmaf(phr, xR, fmaf(phl, xL, y));
-          const f2pair xn = df_add_f(f2pair{xh[i], xlt[i * R]}, d);
-          xh[i] = xn.h;
-          xlt[i * R] = xn.l;
-          maxd = fmaxf(maxd, fabsf(d));
-          maxx = fmaxf(maxx, fabsf(xn.h));
-        }
-      }
+      float maxd = 0.f, maxx = 0.f;
+      if (nrows == TT) backward_update<R, TT, true>(g, cfb, nrows, xL, xR, xh, xlt, maxd, maxx);
+      else backward_update<R, TT, false>(g, cfb, nrows, xL, xR, xh, xlt, maxd, maxx);
       if (adaptive && step >= 1) {   // per-CTA, per-column maxima of |d| and |x| for the test
         if (bl < m) { redD[bl * R + r] = maxd; redX[bl * R + r] = maxx; }
         __syncthreads();
@@ -308,10 +311,13 @@ __global__ void __launch_bounds__(512, 1) k_solve_refined(const __grid_constant_
       }
     }
     // ---- X = xh + xl rounded once to binary64 -------------------------------------
+    if (col_ok) {
+      double* p = X + row0 * a.ldX + col;
 #pragma unroll
-    for (int i = 0; i < TT; i++) {
-      const int64_t row = row0 + i;
-      if (blk_ok && col_ok && row < n) X[row * a.ldX + col] = tdm_f2d(xh[i]) + tdm_f2d(xlt[i * R]);
+      for (int i = 0; i < TT; i++) {
+        if (i < nrows) *p = tdm_f2d(xh[i]) + tdm_f2d(xlt[i * R]);
+        p += a.ldX;
+      }
     }
   }
   cluster_barrier();

@@ -79,10 +79,10 @@ using namespace tdmk;
 
 template <typename T, int R, int TT, int MAXT, bool TMA>
 __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const __grid_constant__ CUtensorMap tmF, const SolveArgs a) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ int wait_ok;
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  unsigned char* base = smem_raw + smem_align_pad(smem_raw);
   T* fbuf = reinterpret_cast<T*>(base);
   T* scf = reinterpret_cast<T*>(base + fbuf_bytes(a.m, TT, R, (int)sizeof(T), TMA));   // [m*t][8]
   const Smem s = carve(reinterpret_cast<unsigned char*>(scf) + coef_bytes(a.m, TT, (int)sizeof(T)), a.m, R,
@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
     if constexpr (TMA) {
       if (!abort && !tdm_mbar_wait_cta(&mbar, phase, a.err, &wait_ok)) abort = true;
       phase ^= 1u;
+      // rows beyond n arrive as zeros (TMA fills out-of-bounds elements with zero)
       const T* src = fbuf + (size_t)bl * TT * R + r;
 #pragma unroll
       for (int i = 0; i < TT; i++) v[i] = blk_ok ? src[i * R] : T(0);
@@ -152,21 +153,13 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
       for (int i = 0; i < TT; i++) v[i] = (i < nrows && col_ok) ? Fp[(int64_t)i * a.ldF] : T(0);
     }
     // A2 + A3 forward: one pass over the rows
-    T bR = T(0), bL = T(0), g = T(0);
-#pragma unroll
-    for (int i = 0; i < TT; i++) {
-      if (i < nrows) {
-        T gr, gl, lf, unused;
-        ld4(scf + (size_t)(bl * TT + i) * kNCOEF, gr, gl, lf, unused);
-        bR = fma(gr, v[i], bR);
-        bL = fma(gl, v[i], bL);
-        g = fma(-lf, g, v[i]);
-        v[i] = g;
-      }
-    }
+    const T* cfb = scf + (size_t)bl * TT * kNCOEF;
+    T bR = T(0), bL = T(0);
+    if (nrows == TT) forward_pass<T, TT, true>(v, cfb, nrows, bR, bL);
+    else forward_pass<T, TT, false>(v, cfb, nrows, bR, bL);
     if (bl < a.m) {
-      reinterpret_cast<T*>(s.betaR)[bl * R + r] = bR;
-      reinterpret_cast<T*>(s.betaL)[bl * R + r] = bL;
+      s.betaR[bl * R + r] = tdm_to_f64<T>(bR);
+      s.betaL[bl * R + r] = tdm_to_f64<T>(bL);
     }
     __syncthreads();
     separator_partials<T, R>(a, s, c, parity);
@@ -176,18 +169,9 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
       if (b >= 1) xL = separator_value<T, R>(s, bl, r);
       if (b + 1 <= a.M - 1) xR = separator_value<T, R>(s, bl + 1, r);
     }
-    T y = T(0);
     T* Xp = X + row0 * a.ldX + col;
-#pragma unroll
-    for (int i = TT - 1; i >= 0; i--) {
-      if (i < nrows) {
-        T cc, invd, phl, phr;
-        ld4(scf + (size_t)(bl * TT + i) * kNCOEF + 4, cc, invd, phl, phr);
-        y = fma(-cc, y, v[i]) * invd;
-        const T x = fma(phr, xR, fma(phl, xL, y));
-        if (col_ok) Xp[(int64_t)i * a.ldX] = x;
-      }
-    }
+    if (nrows == TT) backward_store<T, TT, true>(v, cfb, nrows, xL, xR, Xp, a.ldX, col_ok);
+    else backward_store<T, TT, false>(v, cfb, nrows, xL, xR, Xp, a.ldX, col_ok);
     parity ^= 1;
   }
   // no CTA may leave while a peer can still read its shared memory
