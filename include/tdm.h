@@ -33,6 +33,11 @@
  *  - Invalid arguments are rejected on the host before any launch with
  *    TDM_ERR_INVALID_ARG; nothing is enqueued in that case.
  *  - Handles are not thread-safe: one host thread at a time per handle.
+ *  - Solves may be captured into a CUDA graph.  A captured solve is not
+ *    tracked by tdm_get_info / tdm_destroy; synchronize the graph's stream
+ *    before destroying a plan it uses.  A batched call builds its device work
+ *    list on first use of an argument set (not capturable): call it once with
+ *    the same arguments before capturing it.
  */
 #ifndef TDM_H
 #define TDM_H

@@ -34,6 +34,17 @@ tdm_status validate_solve(const tdm_plan_s* h, const void* F, int64_t ldF, const
   return TDM_OK;
 }
 
+// Records the plan's completion event, except while the stream is being
+// captured into a CUDA graph (the graph's launches are synchronized by the
+// caller; an event recorded inside a capture cannot be waited on afterwards).
+cudaError_t record_last(tdm_plan_s* h, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusNone) return cudaSuccess;
+  return cudaEventRecord(h->last, s);
+}
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -116,9 +127,10 @@ extern "C" tdm_status tdm_solve(tdm_handle h, const void* F, int64_t ldF, void* 
   if (st != TDM_OK || N == 0) return st;
   DeviceGuard g(h->device);
   cudaStream_t s = (cudaStream_t)stream;
+  (void)cudaGetLastError();   // report only errors of this call
   st = tdm_launch_solve(h, F, ldF, X, ldX, N, prec, s);
   if (st != TDM_OK) return st;
-  TDM_CUDA_TRY(cudaEventRecord(h->last, s));
+  TDM_CUDA_TRY(record_last(h, s));
   return TDM_OK;
 }
 
@@ -134,9 +146,10 @@ extern "C" tdm_status tdm_solve_batched(const tdm_handle* hs, int count, const v
   }
   DeviceGuard g(hs[0]->device);
   cudaStream_t s = (cudaStream_t)stream;
+  (void)cudaGetLastError();
   tdm_status st = tdm_launch_batched(const_cast<tdm_plan_s* const*>(hs), count, F, ldF, X, ldX, N, prec, s);
   if (st != TDM_OK) return st;
-  for (int k = 0; k < count; k++) TDM_CUDA_TRY(cudaEventRecord(hs[k]->last, s));
+  for (int k = 0; k < count; k++) TDM_CUDA_TRY(record_last(hs[k], s));
   return TDM_OK;
 }
 
@@ -163,17 +176,19 @@ extern "C" tdm_status tdm_solve_backward(tdm_handle h, const void* W, const void
   if (overlaps(X, bytes, dF, bytes)) return TDM_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   cudaStream_t s = (cudaStream_t)stream;
+  (void)cudaGetLastError();
   st = tdm_launch_solve(h, W, ld, dF, ld, N, prec, s);   // Lambda = A^{-1} W (A = A^T)
   if (st != TDM_OK) return st;
   st = tdm_launch_backward_sums(h, dF, X, ld, N, da, db, prec, s);
   if (st != TDM_OK) return st;
-  TDM_CUDA_TRY(cudaEventRecord(h->last, s));
+  TDM_CUDA_TRY(record_last(h, s));
   return TDM_OK;
 }
 
 extern "C" tdm_status tdm_get_info(tdm_handle h, tdm_info* info) {
   if (!h || !info) return TDM_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
+  (void)cudaGetLastError();
   TDM_CUDA_TRY(cudaEventSynchronize(h->last));
   int err = 0;
   TDM_CUDA_TRY(cudaMemcpy(&err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -28,7 +28,8 @@ enum {
 // Residual coefficients of the refined path, [n][8] binary32:
 // sigma_i = b_i + a_{i-1} + a_i (row sum) and a_i, each split into three
 // binary32 parts whose sum equals the binary64 value (to 2^-72 relative).
-enum { kS0 = 0, kS1 = 1, kS2 = 2, kA0 = 3, kA1 = 4, kA2 = 5, kNRES = 8 };
+// The first 4-vector holds the two leading parts of both (one vector load).
+enum { kS0 = 0, kS1 = 1, kA0 = 2, kA1 = 3, kS2 = 4, kA2 = 5, kNRES = 8 };
 
 // Device status bits written by the prepare kernels.
 enum {
@@ -118,6 +119,7 @@ tdm_status tdm_launch_solve(tdm_plan_s* p, const void* F, int64_t ldF, void* X, 
 tdm_status tdm_launch_backward_sums(tdm_plan_s* p, const void* W, const void* X, int64_t ld,
                                     int64_t N, double* da, double* db, tdm_precision prec,
                                     cudaStream_t s);
+void tdm_batched_forget(const tdm_plan_s* p);
 tdm_status tdm_launch_batched(tdm_plan_s* const* ps, int count, const void* const* F,
                               const int64_t* ldF, void* const* X, const int64_t* ldX,
                               const int64_t* N, tdm_precision prec, cudaStream_t s);

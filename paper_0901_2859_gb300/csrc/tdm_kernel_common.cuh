@@ -222,32 +222,16 @@ __device__ __forceinline__ void separator_partials(const SolveArgs& a, const Sme
   __syncthreads();
 }
 
-// x(p_{b0+j}) for rhs r, in the solve's type
+// x(p_{b0+j}) for rhs r, in the solve's type: LR + LL + piR inR + piL inL
 template <typename T, int R>
-__device__ __forceinline__ T separator_value(const Smem& s, int j, int r);
-template <>
-__device__ __forceinline__ double separator_value<double, 8>(const Smem& s, int j, int r) {
-  return fma(s.piR[j], s.in[r], fma(s.piL[j], s.in[8 + r], s.lr[j * 8 + r] + s.ll[j * 8 + r]));
+__device__ __forceinline__ T separator_value(const Smem& s, int j, int r) {
+  if constexpr (sizeof(T) == 8) {
+    return fma(s.piR[j], s.in[r], fma(s.piL[j], s.in[R + r], s.lr[j * R + r] + s.ll[j * R + r]));
+  } else {
+    const float loc = tdm_d2f(s.lr[j * R + r]) + tdm_d2f(s.ll[j * R + r]);
+    return fmaf(s.piR32[j], s.in32[r], fmaf(s.piL32[j], s.in32[R + r], loc));
+  }
 }
-template <>
-__device__ __forceinline__ double separator_value<double, 16>(const Smem& s, int j, int r) {
-  return fma(s.piR[j], s.in[r], fma(s.piL[j], s.in[16 + r], s.lr[j * 16 + r] + s.ll[j * 16 + r]));
-}
-template <>
-__device__ __forceinline__ double separator_value<double, 32>(const Smem& s, int j, int r) {
-  return fma(s.piR[j], s.in[r], fma(s.piL[j], s.in[32 + r], s.lr[j * 32 + r] + s.ll[j * 32 + r]));
-}
-template <int R>
-__device__ __forceinline__ float separator_value_f32(const Smem& s, int j, int r) {
-  const float loc = tdm_d2f(s.lr[j * R + r]) + tdm_d2f(s.ll[j * R + r]);
-  return fmaf(s.piR32[j], s.in32[r], fmaf(s.piL32[j], s.in32[R + r], loc));
-}
-template <>
-__device__ __forceinline__ float separator_value<float, 8>(const Smem& s, int j, int r) { return separator_value_f32<8>(s, j, r); }
-template <>
-__device__ __forceinline__ float separator_value<float, 16>(const Smem& s, int j, int r) { return separator_value_f32<16>(s, j, r); }
-template <>
-__device__ __forceinline__ float separator_value<float, 32>(const Smem& s, int j, int r) { return separator_value_f32<32>(s, j, r); }
 
 // A2 + A3 over one block held in v[] (overwritten with the forward-eliminated
 // values): the two beta dot products and the local sweep's forward pass.

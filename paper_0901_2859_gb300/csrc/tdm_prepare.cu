@@ -239,8 +239,11 @@ __global__ void k_residual_coefficients(const double* __restrict__ a, const doub
     double sh, sl;
     two_sum(s2, e1 + e2, sh, sl);
     float out[kNRES] = {0, 0, 0, 0, 0, 0, 0, 0};
-    split3(sh, sl, out + kS0);
-    split3(ar, 0.0, out + kA0);
+    float sg[3], av[3];
+    split3(sh, sl, sg);
+    split3(ar, 0.0, av);
+    out[kS0] = sg[0]; out[kS1] = sg[1]; out[kS2] = sg[2];
+    out[kA0] = av[0]; out[kA1] = av[1]; out[kA2] = av[2];
     for (int k = 0; k < kNRES; k++) res32[i * kNRES + k] = out[k];
   }
 }
@@ -262,7 +265,9 @@ extern "C" tdm_status tdm_destroy(tdm_handle h) {
   cudaGetDevice(&cur);
   cudaSetDevice(h->device);
   if (h->last) cudaEventSynchronize(h->last);
+  tdm_batched_forget(h);
   tdm_free_plan(h);
+  (void)cudaGetLastError();   // leave no error behind for the next call
   cudaSetDevice(cur);
   return TDM_OK;
 }
@@ -282,6 +287,7 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
   if (t != 16 && t != 32) return TDM_ERR_INVALID_ARG;
   if (steps < 0 || steps > 4) return TDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  (void)cudaGetLastError();   // report only errors of this call
 
   tdm_plan_s* p = new tdm_plan_s();
   p->n = n;

@@ -1,27 +1,35 @@
 // tdm_refine.cu -- binary32 dichotomy solves with iterative refinement: F in
-// binary32, X in binary64, accuracy of a binary64 solve (or better).
+// binary32, X in binary64, accuracy of a binary64 solve (or better); one
+// persistent kernel that serves a single series (tdm_solve) and many series of
+// different sizes (tdm_solve_batched).
 //
-// Per tile of R right-hand sides (a cluster owns all n rows, as in the plain
-// solve), with the tile's F kept in shared memory and the iterate x held in
-// registers as a binary32 pair (x = xh + xl, ~48 significant bits):
+// Work items.  An item is one tile of R right-hand sides of one series
+// A X = F.  A thread-block cluster processes one item at a time with all n rows
+// (CTA c owns m blocks of t rows, thread (block, rhs) owns one block for one
+// right-hand side) and walks a list of items; consecutive items of a cluster
+// normally belong to the same series.  Per item:
 //
 //   x  = solve32(F)                                   (steps A2-A5, binary32)
-//   repeat k times:
+//   repeat (adaptive, at most 4 times, or a fixed count):
 //     r_i = F_i - (A x)_i                             (error-free, see below)
 //     x  += solve32(r)
 //   X_i = xh_i + xl_i rounded once to binary64.
 //
+// x is held as a binary32 pair: high words in registers, low words in shared
+// memory.  F is read from global memory for the first solve and again (from
+// L2) for each residual, so shared memory holds no copy of the tile and two
+// CTAs fit on an SM.
+//
 // The residual is formed in row-sum form.  With sigma_i = b_i + a_{i-1} + a_i
 // and the fluxes E_i = a_i (x_{i+1} - x_i),
 //     (A x)_i = sigma_i x_i - E_{i-1} + E_i,
-// so  r_i = F_i - sigma_i x_i + E_{i-1} - E_i.  For the weakly dominant,
-// ill-conditioned series of Section 4 the fluxes are small next to A's
-// entries times x, the differences x_{i+1} - x_i are formed exactly from the
-// pair representation, and the large terms E_{i-1} - E_i cancel exactly in
-// Knuth's TwoSum; the residual's absolute error stays near 2^-48 |E| instead of
-// 2^-24 |A||x|.  No binary64 instruction is issued per unknown except the
-// final rounding of xh + xl.  Iterative refinement itself is not part of the
-// paper's method; its correction solves are the paper's method in binary32.
+// so  r_i = F_i - sigma_i x_i + E_{i-1} - E_i.  The differences x_{i+1} - x_i
+// are formed exactly from the pair representation and the large terms
+// E_{i-1} - E_i cancel exactly in Knuth's TwoSum, so the residual's absolute
+// error stays near 2^-48 |E| instead of 2^-24 |A||x|.  No binary64
+// instruction is issued per unknown except the final rounding of xh + xl.
+// Iterative refinement itself is not part of the paper's method; its
+// correction solves are the paper's method in binary32.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -29,30 +37,15 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "tdm_df.cuh"
 #include "tdm_kernel_common.cuh"
+#include "tdm_refine.cuh"
 #include "tdm_tma.cuh"
 
 namespace {
 using namespace tdmk;
-
-struct RefineArgs {
-  SolveArgs s;        // F (binary32), X (binary64), coefficients (binary32)
-  const float* res;   // [n][8] residual coefficients: sigma and a split in binary32 parts
-  int steps;          // refinement steps after the first solve
-};
-
-__host__ __device__ inline size_t refine_smem_bytes(int m, int t, int R) {
-  const int rows = m * t;
-  return 128 + (size_t)rows * R * 4          // F tile
-         + (size_t)rows * R * 4              // low words of the iterate
-         + (size_t)rows * kNCOEF * 4         // solve coefficients
-         + (size_t)(rows + 1) * 4 * 4        // residual coefficients (sigma_h, sigma_l, a_h, a_l)
-         + (size_t)4 * m * R * 4             // block edge values of x (first/last row, hi/lo)
-         + (size_t)2 * m * R * 4 + 4 * R * 4 // convergence maxima (per block, per CTA x2 parity)
-         + smem_bytes(m, t, R, 4, false) - 128 - coef_bytes(m, t, 4);
-}
 
 // Estimated relative error left after a correction d_k: ratio_k^2 / ratio_{k-1}
 // (linear convergence), with ratio_k = max over columns of max|d_k| / max|x|;
@@ -80,10 +73,49 @@ __device__ __forceinline__ float cluster_ratio(const float* slot, int C, int tid
   return *bcast;
 }
 
+// streaming loads/stores for the right-hand sides and the solution: they are
+// touched once per tile and must not evict the coefficients from L1
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_stream(double* p, double v) {
+  asm volatile("st.global.cs.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void ldg4(const float* p, float& x, float& y, float& z, float& w) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  x = v.x; y = v.y; z = v.z; w = v.w;
+}
+
+// 4 coefficients from shared memory (SM = true) or through the read-only cache
+template <bool SM>
+__device__ __forceinline__ void cld4(const float* p, float& x, float& y, float& z, float& w) {
+  if constexpr (SM) ld4(p, x, y, z, w);
+  else ldg4(p, x, y, z, w);
+}
+
+// forward pass (A2 + A3)
+template <int TT, bool FULL, bool SM>
+__device__ __forceinline__ void forward_pass_g(float (&v)[TT], const float* cf, int nrows, float& bR, float& bL) {
+  float g = 0.f;
+#pragma unroll
+  for (int i = 0; i < TT; i++) {
+    if (FULL || i < nrows) {
+      float gr, gl, lf, unused;
+      cld4<SM>(cf + i * kNCOEF, gr, gl, lf, unused);
+      bR = fmaf(gr, v[i], bR);
+      bL = fmaf(gl, v[i], bL);
+      g = fmaf(-lf, g, v[i]);
+      v[i] = g;
+    }
+  }
+}
+
 // A5 of a correction solve: back substitution, correction with the separator
 // values, and x += d in pair arithmetic (high words in registers, low words in
 // shared memory at stride R); tracks max|d| and max|x| for the convergence test.
-template <int R, int TT, bool FULL>
+template <int R, int TT, bool FULL, bool SM>
 __device__ __forceinline__ void backward_update(const float (&g)[TT], const float* cf, int nrows, float xL,
                                                 float xR, float (&xh)[TT], float* xlt, float& maxd,
                                                 float& maxx) {
@@ -92,7 +124,7 @@ __device__ __forceinline__ void backward_update(const float (&g)[TT], const floa
   for (int i = TT - 1; i >= 0; i--) {
     if (FULL || i < nrows) {
       float cc, invd, phl, phr;
-      ld4(cf + i * kNCOEF + 4, cc, invd, phl, phr);
+      cld4<SM>(cf + i * kNCOEF + 4, cc, invd, phl, phr);
       y = fmaf(-cc, y, g[i]) * invd;
       const float d = fmaf(phr, xR, fmaf(phl, xL, y));
       const f2pair xn = df_add_f(f2pair{xh[i], xlt[i * R]}, d);
@@ -104,113 +136,101 @@ __device__ __forceinline__ void backward_update(const float (&g)[TT], const floa
   }
 }
 
-template <int R, int TT, bool TMA>
-__global__ void __launch_bounds__(512, 1) k_solve_refined(const __grid_constant__ CUtensorMap tmF, const RefineArgs ra) {
-  const SolveArgs& a = ra.s;
+template <int R, int TT, int NT, int MINB, bool SM>
+__global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ int wait_ok;
   __shared__ float ratio_s;
-  const int m = a.m;
+  const int m = L.m;
   const int rows_cta = m * TT;
-  unsigned char* base = smem_raw + smem_align_pad(smem_raw);
-  float* fbuf = reinterpret_cast<float*>(base);                         // [rows_cta][R]  F tile
-  float* sxl = fbuf + (size_t)rows_cta * R;                             // [rows_cta][R]  low words of x
-  float* scf = sxl + (size_t)rows_cta * R;                              // [rows_cta][8]
-  float* sres = scf + (size_t)rows_cta * kNCOEF;                        // [rows_cta + 1][4]
-  float* eFh = sres + (size_t)(rows_cta + 1) * 4;                       // [m][R] first-row x, hi
+  unsigned char* p = smem_raw + smem_align_pad(smem_raw);
+  float* sxl = reinterpret_cast<float*>(p); p += round16((size_t)rows_cta * R * 4);   // [rows_cta][R]
+  float* eFh = reinterpret_cast<float*>(p); p += round16((size_t)4 * m * R * 4);     // edges [4][m][R]
   float* eFl = eFh + m * R;
-  float* eLh = eFl + m * R;                                             // [m][R] last-row x, hi
+  float* eLh = eFl + m * R;
   float* eLl = eLh + m * R;
-  float* redD = eLl + m * R;                                            // [m][R] max |d| per block
-  float* redX = redD + m * R;                                           // [m][R] max |x| per block
-  float* cvg = redX + m * R;                                            // [2 parity][2][R] per CTA, read remotely
-  const Smem s = carve(reinterpret_cast<unsigned char*>(cvg + 4 * R), m, R, 4);
+  float* redD = reinterpret_cast<float*>(p); p += round16((size_t)2 * m * R * 4);    // [m][R]
+  float* redX = redD + m * R;
+  float* cvg = reinterpret_cast<float*>(p); p += round16((size_t)4 * R * 4);         // [2][2][R]
+  // SM: the CTA's coefficient rows, reloaded when the series changes
+  float* scf = reinterpret_cast<float*>(p); if (SM) p += round16((size_t)rows_cta * kNCOEF * 4);   // [rows][8]
+  float* sres = reinterpret_cast<float*>(p); if (SM) p += round16((size_t)(rows_cta + 1) * 4 * 4);  // [rows+1][4]
+  const Smem s = carve(p, m, R, 4);
 
   const unsigned c = cluster_rank();
   const int tid = threadIdx.x;
   const int r = tid % R;
   const int bl = tid / R;
-  const int b = (int)c * m + bl;
-  const bool blk_ok = (bl < m) && (b < a.M);
-  const int64_t row0 = (int64_t)b * TT;
-  const int nrows = blk_ok ? (int)((a.n - row0) < TT ? (a.n - row0) : TT) : 0;   // rows that exist
-  const int64_t cta_row0 = (int64_t)c * rows_cta;
-  const int n = a.n;
-  const float* __restrict__ coef = static_cast<const float*>(a.coef);
-  double* __restrict__ X = static_cast<double*>(a.X);
-  // steps > 0: exactly that many corrections; otherwise adaptive with a cap of 4
-  const bool adaptive = ra.steps <= 0;
-  const int cap = adaptive ? 4 : ra.steps;
+  const int cluster_id = blockIdx.x / L.C;
+  const int nclusters = gridDim.x / L.C;
+  float* xlt = sxl + (size_t)bl * TT * R + r;   // this thread's low words (valid when bl < m)
 
-  setup_ratios(a, s, c);
-  for (int k = tid; k < rows_cta * kNCOEF / 4; k += blockDim.x) {
-    const int64_t row = cta_row0 + (k * 4) / kNCOEF;
-    float x = 0.f, y = 0.f, z = 0.f, w = 0.f;
-    if (row < n) ld4(coef + cta_row0 * kNCOEF + (int64_t)k * 4, x, y, z, w);
-    float* d = scf + (size_t)k * 4;
-    d[0] = x; d[1] = y; d[2] = z; d[3] = w;
-  }
-  for (int k = tid; k <= rows_cta; k += blockDim.x) {   // rows cta_row0-1 .. cta_row0+rows_cta-1
-    const int64_t row = cta_row0 - 1 + k;
-    float sh = 0.f, sl = 0.f, ah = 0.f, al = 0.f;
-    if (row >= 0 && row < n) {
-      const float* q = ra.res + row * kNRES;
-      sh = q[kS0]; sl = q[kS1]; ah = q[kA0]; al = q[kA1];
-    }
-    float* d = sres + (size_t)k * 4;
-    d[0] = sh; d[1] = sl; d[2] = ah; d[3] = al;
-  }
-  if (TMA && tid == 0) tdm_mbar_init(&mbar, 1);
-  __syncthreads();
-
-  const int cluster_id = blockIdx.x / a.C;
-  const int nclusters = gridDim.x / a.C;
-  const uint32_t tile_bytes = (uint32_t)rows_cta * R * 4;
-  const int nbox = rows_cta / a.box_rows;
-  auto issue = [&](int tile) {
-    tdm_mbar_expect_tx(&mbar, tile_bytes);
-    for (int k = 0; k < nbox; k++)
-      tdm_tma_load_2d(fbuf + (size_t)k * a.box_rows * R, &tmF, tile * R, (int)(cta_row0 + (int64_t)k * a.box_rows),
-                      &mbar);
-  };
-  if (TMA && tid == 0 && cluster_id < a.ntiles) issue(cluster_id);
-
-  uint32_t phase = 0u;
-  bool abort = false;
+  SolveArgs a;   // per-series view used by the shared step-A4 code
+  memset(&a, 0, sizeof(a));
+  a.m = m;
+  a.C = L.C;
+  a.err = L.err;
+  int cur_series = -1;
   int parity = 0;
-  for (int tile = cluster_id; tile < a.ntiles; tile += nclusters) {
-    const int64_t col = (int64_t)tile * R + r;
-    const bool col_ok = col < a.N;
-    if constexpr (TMA) {
-      if (!abort && !tdm_mbar_wait_cta(&mbar, phase, a.err, &wait_ok)) abort = true;
-      phase ^= 1u;
-    } else {   // direct coalesced loads into the tile buffer
-      const float* __restrict__ F = static_cast<const float*>(a.F);
-      float* dst = fbuf + (size_t)bl * TT * R + r;
-#pragma unroll 4
-      for (int i = 0; i < TT; i++) {
-        const int64_t row = row0 + i;
-        if (bl < m) dst[i * R] = (blk_ok && col_ok && row < n) ? F[row * a.ldF + col] : 0.f;
+
+  for (int it = cluster_id; it < L.nitems; it += nclusters) {
+    const RefItem& item = L.single ? L.one : L.items[it];
+    const int tile = L.single ? it : item.tile;
+    if (item.series != cur_series) {   // new series: ratios and prefix products
+      __syncthreads();
+      a.M = item.M;
+      a.n = item.n;
+      a.rR = item.rR;
+      a.rL = item.rL;
+      setup_ratios(a, s, c);
+      if constexpr (SM) {
+        const int64_t cta_row0 = (int64_t)c * rows_cta;
+        for (int k = tid; k < rows_cta * kNCOEF / 4; k += blockDim.x) {
+          const int64_t row = cta_row0 + (k * 4) / kNCOEF;
+          float x = 0.f, y = 0.f, z = 0.f, w = 0.f;
+          if (row < item.n) ldg4(item.coef + cta_row0 * kNCOEF + (int64_t)k * 4, x, y, z, w);
+          float* d = scf + (size_t)k * 4;
+          d[0] = x; d[1] = y; d[2] = z; d[3] = w;
+        }
+        for (int k = tid; k <= rows_cta; k += blockDim.x) {   // rows cta_row0-1 .. cta_row0+rows_cta-1
+          const int64_t row = cta_row0 - 1 + k;
+          float x = 0.f, y = 0.f, z = 0.f, w = 0.f;
+          if (row >= 0 && row < item.n) ldg4(item.res + row * kNRES, x, y, z, w);   // kS0, kS1, kA0, kA1
+          float* d = sres + (size_t)k * 4;
+          d[0] = x; d[1] = y; d[2] = z; d[3] = w;
+        }
       }
       __syncthreads();
+      cur_series = item.series;
     }
-    const float* Ft = fbuf + (size_t)bl * TT * R + r;
-    float* xlt = sxl + (size_t)bl * TT * R + r;   // this thread's low words, stride R
+    const int n = item.n;
+    const int b = (int)c * m + bl;
+    const bool blk_ok = (bl < m) && (b < item.M);
+    const int64_t row0 = (int64_t)b * TT;
+    const int nrows = blk_ok ? (int)((n - row0) < TT ? (n - row0) : TT) : 0;
+    const int64_t col = (int64_t)tile * R + r;
+    const bool col_ok = col < item.N;
+    const bool active = nrows > 0 && col_ok;   // this thread's rows and column exist
+    const float* Fp = item.F + row0 * item.ldF + col;
+    // this block's coefficient rows (rsb[-1] is the row before the block)
+    const float* cfb = SM ? scf + (size_t)bl * TT * kNCOEF : item.coef + row0 * kNCOEF;
+    const float* rsb = SM ? sres + (size_t)(bl * TT + 1) * 4 : item.res + row0 * kNRES;
+    constexpr int RS = SM ? 4 : kNRES;   // stride of the residual coefficient rows
+    const bool adaptive = item.steps <= 0;
+    const int cap = adaptive ? 4 : item.steps;
 
     float xh[TT], g[TT];
 #pragma unroll
-    for (int i = 0; i < TT; i++) { xh[i] = 0.f; if (bl < m) xlt[i * R] = 0.f; }
+    for (int i = 0; i < TT; i++) {
+      xh[i] = 0.f;
+      if (bl < m) xlt[i * R] = 0.f;
+      g[i] = (active && i < nrows) ? ld_stream(Fp + (int64_t)i * item.ldF) : 0.f;
+    }
 
     float ratio_prev = 1.f;
     int cpar = 0;
     for (int step = 0;; step++) {
-      if (step == 0) {
-#pragma unroll
-        for (int i = 0; i < TT; i++) g[i] = blk_ok ? Ft[i * R] : 0.f;   // zeros beyond n
-      } else {
+      if (step > 0) {
         // ---- residual r = F - A x of the current iterate ------------------------
-        // (threads beyond the CTA's m blocks only take part in the barriers)
         if (bl < m) {
           eFh[bl * R + r] = xh[0]; eFl[bl * R + r] = xlt[0];
           eLh[bl * R + r] = xh[TT - 1]; eLl[bl * R + r] = xlt[(TT - 1) * R];
@@ -219,54 +239,55 @@ __global__ void __launch_bounds__(512, 1) k_solve_refined(const __grid_constant_
         if (adaptive && step >= 2) {   // converged after the previous correction?
           // after the first correction there is no contraction estimate yet: stop only if
           // the correction itself is below the tolerance
-          const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, a.C, tid, &ratio_s);
+          const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, L.C, tid, &ratio_s);
           const bool stop = (step == 2) ? (ratio <= kRefineTol) : (ratio * ratio <= kRefineTol * ratio_prev);
           ratio_prev = ratio;
           if (stop) break;
         }
-        if (bl >= m) {
+        if (bl < m) {
 #pragma unroll
-          for (int i = 0; i < TT; i++) g[i] = 0.f;
-        } else {
-        f2pair xm{0.f, 0.f}, xp{0.f, 0.f};   // x at rows row0-1 and row0+TT
-        if (bl > 0) {
-          xm = f2pair{eLh[(bl - 1) * R + r], eLl[(bl - 1) * R + r]};
-        } else if (c > 0) {
-          xm = f2pair{ld_cluster_f32(eLh + (m - 1) * R + r, c - 1), ld_cluster_f32(eLl + (m - 1) * R + r, c - 1)};
-        }
-        if (bl < m - 1) {
-          xp = f2pair{eFh[(bl + 1) * R + r], eFl[(bl + 1) * R + r]};
-        } else if ((int)c < a.C - 1) {
-          xp = f2pair{ld_cluster_f32(eFh + r, c + 1), ld_cluster_f32(eFl + r, c + 1)};
-        }
-        // flux into the first row: E_{row0-1} = a_{row0-1} (x_row0 - x_{row0-1})
-        const float* rc = sres + (size_t)(bl * TT) * 4;   // row0-1 at index bl*TT
-        f2pair xi{xh[0], xlt[0]};
-        f2pair Ep = df_mul(f2pair{rc[2], rc[3]}, df_diff(xi, xm));
+          for (int i = 0; i < TT; i++) g[i] = (active && i < nrows) ? ld_stream(Fp + (int64_t)i * item.ldF) : 0.f;
+          f2pair xm{0.f, 0.f}, xp{0.f, 0.f};   // x at rows row0-1 and row0+TT
+          if (bl > 0) {
+            xm = f2pair{eLh[(bl - 1) * R + r], eLl[(bl - 1) * R + r]};
+          } else if (c > 0) {
+            xm = f2pair{ld_cluster_f32(eLh + (m - 1) * R + r, c - 1), ld_cluster_f32(eLl + (m - 1) * R + r, c - 1)};
+          }
+          if (bl < m - 1) {
+            xp = f2pair{eFh[(bl + 1) * R + r], eFl[(bl + 1) * R + r]};
+          } else if ((int)c < L.C - 1) {
+            xp = f2pair{ld_cluster_f32(eFh + r, c + 1), ld_cluster_f32(eFl + r, c + 1)};
+          }
+          if (nrows > 0) {
+            // flux into the first row: E_{row0-1} = a_{row0-1} (x_row0 - x_{row0-1})
+            float a_h = 0.f, a_l = 0.f;
+            if (row0 > 0) { a_h = rsb[-RS + kA0]; a_l = rsb[-RS + kA1]; }
+            f2pair xi{xh[0], xlt[0]};
+            f2pair Ep = df_mul(f2pair{a_h, a_l}, df_diff(xi, xm));
 #pragma unroll
-        for (int i = 0; i < TT; i++) {
-          float sh, sl, ah, al;
-          ld4(rc + (i + 1) * 4, sh, sl, ah, al);
-          const f2pair xn = (i + 1 < TT) ? f2pair{xh[i + 1], xlt[(i + 1) * R]} : xp;
-          const f2pair E = df_mul(f2pair{ah, al}, df_diff(xn, xi));
-          const f2pair S = df_mul(f2pair{sh, sl}, xi);
-          const float Fi = Ft[i * R];   // bl < m here; rows beyond n hold zeros
-          const f2pair w = two_sum_f(Ep.h, -E.h);
-          const f2pair u = two_sum_f(Fi, w.h);
-          const f2pair v = two_sum_f(u.h, -S.h);
-          const float small = ((Ep.l - E.l) - S.l) + (w.l + u.l + v.l);
-          g[i] = v.h + small;
-          Ep = E;
-          xi = xn;
-        }
+            for (int i = 0; i < TT; i++) {
+              // rows beyond n carry zero coefficients and zero iterate, so they add nothing
+              float sh = 0.f, sl = 0.f, ah = 0.f, al = 0.f;
+              if (i < nrows) cld4<SM>(rsb + i * RS, sh, sl, ah, al);   // kS0, kS1, kA0, kA1
+              const f2pair xn = (i + 1 < TT) ? f2pair{xh[i + 1], xlt[(i + 1) * R]} : xp;
+              const f2pair E = df_mul(f2pair{ah, al}, df_diff(xn, xi));
+              const f2pair S = df_mul(f2pair{sh, sl}, xi);
+              const float Fi = g[i];
+              const f2pair w = two_sum_f(Ep.h, -E.h);
+              const f2pair u = two_sum_f(Fi, w.h);
+              const f2pair v = two_sum_f(u.h, -S.h);
+              const float small = ((Ep.l - E.l) - S.l) + (w.l + u.l + v.l);
+              g[i] = v.h + small;
+              Ep = E;
+              xi = xn;
+            }
+          }
         }
       }
-
       // ---- binary32 dichotomy solve of g (A2-A5) ---------------------------------
-      const float* cfb = scf + (size_t)bl * TT * kNCOEF;
       float bR = 0.f, bL = 0.f;
-      if (nrows == TT) forward_pass<float, TT, true>(g, cfb, nrows, bR, bL);
-      else forward_pass<float, TT, false>(g, cfb, nrows, bR, bL);
+      if (nrows == TT) forward_pass_g<TT, true, SM>(g, cfb, nrows, bR, bL);
+      else forward_pass_g<TT, false, SM>(g, cfb, nrows, bR, bL);
       if (bl < m) {
         s.betaR[bl * R + r] = tdm_f2d(bR);
         s.betaL[bl * R + r] = tdm_f2d(bL);
@@ -277,11 +298,12 @@ __global__ void __launch_bounds__(512, 1) k_solve_refined(const __grid_constant_
       float xL = 0.f, xR = 0.f;
       if (blk_ok) {
         if (b >= 1) xL = separator_value<float, R>(s, bl, r);
-        if (b + 1 <= a.M - 1) xR = separator_value<float, R>(s, bl + 1, r);
+        if (b + 1 <= item.M - 1) xR = separator_value<float, R>(s, bl + 1, r);
       }
       float maxd = 0.f, maxx = 0.f;
-      if (nrows == TT) backward_update<R, TT, true>(g, cfb, nrows, xL, xR, xh, xlt, maxd, maxx);
-      else backward_update<R, TT, false>(g, cfb, nrows, xL, xR, xh, xlt, maxd, maxx);
+      if (nrows == TT) backward_update<R, TT, true, SM>(g, cfb, nrows, xL, xR, xh, xlt, maxd, maxx);
+      else backward_update<R, TT, false, SM>(g, cfb, nrows, xL, xR, xh, xlt, maxd, maxx);
+      if (!col_ok) maxd = maxx = 0.f;   // padding columns of a ragged tile do not vote
       if (adaptive && step >= 1) {   // per-CTA, per-column maxima of |d| and |x| for the test
         if (bl < m) { redD[bl * R + r] = maxd; redX[bl * R + r] = maxx; }
         __syncthreads();
@@ -296,86 +318,64 @@ __global__ void __launch_bounds__(512, 1) k_solve_refined(const __grid_constant_
       if (step == cap) {
         if (adaptive) {   // cap reached: record whether the last correction met the test
           cluster_barrier();
-          const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, a.C, tid, &ratio_s);
-          if (tid == 0 && !(ratio * ratio <= kRefineTol * ratio_prev)) atomicExch(a.err, kDevErrNotConverged);
+          const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, L.C, tid, &ratio_s);
+          if (tid == 0 && !(ratio * ratio <= kRefineTol * ratio_prev)) atomicExch(L.err, kDevErrNotConverged);
         }
         break;
       }
     }
-    // this tile's F is no longer read: start loading the next tile
-    if constexpr (TMA) {
-      __syncthreads();
-      if (tid == 0 && !abort && tile + nclusters < a.ntiles) {
-        tdm_fence_proxy_async();
-        issue(tile + nclusters);
-      }
-    }
     // ---- X = xh + xl rounded once to binary64 -------------------------------------
-    if (col_ok) {
-      double* p = X + row0 * a.ldX + col;
+    if (active) {
+      double* Xp = item.X + row0 * item.ldX + col;
 #pragma unroll
-      for (int i = 0; i < TT; i++) {
-        if (i < nrows) *p = tdm_f2d(xh[i]) + tdm_f2d(xlt[i * R]);
-        p += a.ldX;
-      }
+      for (int i = 0; i < TT; i++)
+        if (i < nrows) st_stream(Xp + (int64_t)i * item.ldX, tdm_f2d(xh[i]) + tdm_f2d(xlt[i * R]));
     }
   }
+  // no CTA may leave while a peer can still read its shared memory
   cluster_barrier();
 }
 
-struct RCfg {
-  int R = 16, m = 0, C = 0, threads = 0, box_rows = 0;
-  size_t smem = 0;
-};
-
-bool choose_rcfg(int M, int t, RCfg& cfg) {
-  for (int R : {16, 8}) {
-    const int m_max = 512 / R;
-    const int C = (M + m_max - 1) / m_max;
-    if (C > 16) continue;
-    const int m = (M + C - 1) / C;
-    int threads = ((m * R + 31) / 32) * 32;
-    if (threads < 96) threads = 96;
-    int g = 1;
-    for (int d = 1; d <= m; d++)
-      if (m % d == 0 && d * t <= 256) g = d;
-    cfg.R = R; cfg.m = m; cfg.C = C; cfg.threads = threads; cfg.box_rows = g * t;
-    cfg.smem = refine_smem_bytes(m, t, R);
-    if (cfg.smem > 227 * 1024) continue;
-    return true;
-  }
-  return false;
+// shared memory of one CTA (after 128-byte alignment)
+size_t refine_smem_bytes(int m, int t, int R, bool sm_coef) {
+  const int rows = m * t;
+  return 128 + round16((size_t)rows * R * 4)   // low words of the iterate
+         + (sm_coef ? round16((size_t)rows * kNCOEF * 4) + round16((size_t)(rows + 1) * 16) : 0)
+         + round16((size_t)4 * m * R * 4)      // block edge values of x (first/last row, hi/lo)
+         + round16((size_t)2 * m * R * 4)      // per-block convergence maxima
+         + round16((size_t)4 * R * 4)          // per-CTA maxima, 2 parities, read remotely
+         + smem_bytes(m, t, R, 4, false) - 128 - coef_bytes(m, t, 4);
 }
 
-template <int R, int TT, bool TMA>
-tdm_status launch_refined(const CUtensorMap& map, const RefineArgs& args, const RCfg& cfg, cudaStream_t s) {
-  auto kern = k_solve_refined<R, TT, TMA>;
+template <int R, int TT, int NT, int MINB, bool SM>
+tdm_status launch_shape(const RefShape& sh, const RefLaunch& L, int nitems, cudaStream_t s) {
+  auto kern = k_refined<R, TT, NT, MINB, SM>;
   static std::mutex mu;
-  static std::map<std::tuple<int, int, size_t, int>, int> occ;
+  static std::map<std::tuple<int, int, size_t, int>, int> occ;   // (device, C, smem, threads) -> clusters
   int dev = 0;
   cudaGetDevice(&dev);
-  TDM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
-  if (cfg.C > 8) TDM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  TDM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem));
+  if (sh.C > 8) TDM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = cfg.C;
+  at[0].val.clusterDim.x = sh.C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
-  lc.blockDim = dim3(cfg.threads);
-  lc.dynamicSmemBytes = cfg.smem;
+  lc.blockDim = dim3(sh.threads);
+  lc.dynamicSmemBytes = sh.smem;
   lc.stream = s;
   lc.attrs = at;
   lc.numAttrs = 1;
   int maxc = 0;
   {
     std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_tuple(dev, cfg.C, cfg.smem, cfg.threads);
+    auto key = std::make_tuple(dev, sh.C, sh.smem, sh.threads);
     auto it = occ.find(key);
     if (it != occ.end()) {
       maxc = it->second;
     } else {
-      lc.gridDim = dim3(cfg.C);
+      lc.gridDim = dim3(sh.C);
       if (cudaOccupancyMaxActiveClusters(&maxc, (void*)kern, &lc) != cudaSuccess || maxc < 1) {
         (void)cudaGetLastError();
         maxc = 1;
@@ -383,38 +383,81 @@ tdm_status launch_refined(const CUtensorMap& map, const RefineArgs& args, const 
       occ[key] = maxc;
     }
   }
-  const int nclusters = args.s.ntiles < maxc ? args.s.ntiles : maxc;
-  lc.gridDim = dim3(nclusters * cfg.C);
-  TDM_CUDA_TRY(cudaLaunchKernelEx(&lc, kern, map, args));
+  const int nclusters = nitems < maxc ? nitems : maxc;
+  lc.gridDim = dim3(nclusters * sh.C);
+  TDM_CUDA_TRY(cudaLaunchKernelEx(&lc, kern, L));
   return TDM_OK;
 }
 
 }  // namespace
 
-tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX,
-                              int64_t N, cudaStream_t s) {
-  RCfg cfg;
-  if (!choose_rcfg(p->M, p->t, cfg)) return TDM_ERR_NOT_IMPLEMENTED;
-  CUtensorMap map;
-  memset(&map, 0, sizeof(map));
-  const bool tma = getenv("TDM_NO_TMA") == nullptr &&
-                   tdm_encode_tma_2d(&map, F, false, (uint64_t)N, (uint64_t)p->n, (uint64_t)ldF * 4,
-                                     (uint32_t)cfg.R, (uint32_t)cfg.box_rows);
-  RefineArgs args;
-  SolveArgs& a = args.s;
-  a.F = F; a.X = X; a.ldF = ldF; a.ldX = ldX; a.N = N;
-  a.coef = p->coef32;
-  a.rR = p->rR; a.rL = p->rL; a.err = p->dev_err;
-  a.n = (int)p->n; a.M = p->M; a.m = cfg.m; a.C = cfg.C;
-  a.ntiles = (int)((N + cfg.R - 1) / cfg.R);
-  a.box_rows = cfg.box_rows;
-  args.res = p->res32;
-  args.steps = p->refine_steps;
-  switch (cfg.R * 100 + p->t) {
-    case 1632: return tma ? launch_refined<16, 32, true>(map, args, cfg, s) : launch_refined<16, 32, false>(map, args, cfg, s);
-    case 1616: return tma ? launch_refined<16, 16, true>(map, args, cfg, s) : launch_refined<16, 16, false>(map, args, cfg, s);
-    case 832: return tma ? launch_refined<8, 32, true>(map, args, cfg, s) : launch_refined<8, 32, false>(map, args, cfg, s);
-    case 816: return tma ? launch_refined<8, 16, true>(map, args, cfg, s) : launch_refined<8, 16, false>(map, args, cfg, s);
+// Tile shapes: R right-hand sides per tile, NT threads per CTA, m = NT / R
+// blocks per CTA.  R = 8 with 256 threads lets two CTAs share an SM (n up to
+// 16 * 32 * t rows); R = 4 with 512 threads reaches 4 times further (n up to
+// 65536 for t = 32); R = 16 with 512 threads is selectable for experiments.
+bool tdm_refined_shape(int M, int t, RefShape& sh) {
+  const char* env = getenv("TDM_REFINE_R");
+  const int pref = env ? atoi(env) : 8;
+  const int cand[3][2] = {{pref, pref == 8 ? 256 : 512}, {8, 256}, {4, 512}};
+  for (const auto& cr : cand) {
+    const int R = cr[0], NT = cr[1];
+    if (R != 4 && R != 8 && R != 16) continue;
+    const int m_max = NT / R;
+    const int C = (M + m_max - 1) / m_max;
+    if (C > 16) continue;
+    const int m = (M + C - 1) / C;
+    sh.R = R; sh.NT = NT; sh.m = m; sh.C = C;
+    sh.threads = ((m * R + 31) / 32) * 32;
+    if (sh.threads < 96) sh.threads = 96;
+    sh.sm_coef = R != 4;
+    sh.smem = refine_smem_bytes(m, t, R, sh.sm_coef);
+    if (sh.smem > 227 * 1024) continue;
+    return true;
+  }
+  return false;
+}
+
+tdm_status tdm_refined_launch(const RefShape& sh, int t, const RefItem* items, const RefItem* one, int nitems,
+                              int* err, cudaStream_t s) {
+  if (nitems <= 0) return TDM_OK;
+  RefLaunch L;
+  memset(&L, 0, sizeof(L));
+  L.items = items;
+  if (one) L.one = *one;
+  L.nitems = nitems;
+  L.single = items ? 0 : 1;
+  L.m = sh.m;
+  L.C = sh.C;
+  L.err = err;
+  const int key = sh.R * 10000 + sh.NT * 10 + (t == 16 ? 1 : 0);
+  switch (key) {
+    case 8 * 10000 + 256 * 10 + 0: return launch_shape<8, 32, 256, 2, true>(sh, L, nitems, s);
+    case 4 * 10000 + 512 * 10 + 0: return launch_shape<4, 32, 512, 1, false>(sh, L, nitems, s);
+    case 16 * 10000 + 512 * 10 + 0: return launch_shape<16, 32, 512, 1, true>(sh, L, nitems, s);
+    case 8 * 10000 + 256 * 10 + 1: return launch_shape<8, 16, 256, 2, true>(sh, L, nitems, s);
+    case 4 * 10000 + 512 * 10 + 1: return launch_shape<4, 16, 512, 1, false>(sh, L, nitems, s);
+    case 16 * 10000 + 512 * 10 + 1: return launch_shape<16, 16, 512, 1, true>(sh, L, nitems, s);
   }
   return TDM_ERR_NOT_IMPLEMENTED;
+}
+
+RefItem tdm_refined_item(const tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX, int64_t N,
+                         int series) {
+  RefItem it;
+  memset(&it, 0, sizeof(it));
+  it.F = F; it.X = X; it.ldF = ldF; it.ldX = ldX;
+  it.coef = p->coef32; it.res = p->res32; it.rR = p->rR; it.rL = p->rL;
+  it.n = (int)p->n; it.M = p->M; it.N = (int)N; it.tile = 0;
+  it.series = series;
+  it.steps = p->refine_steps;
+  return it;
+}
+
+tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX, int64_t N,
+                              cudaStream_t s) {
+  RefShape sh;
+  if (!tdm_refined_shape(p->M, p->t, sh)) return TDM_ERR_NOT_IMPLEMENTED;
+  const RefItem one = tdm_refined_item(p, F, ldF, X, ldX, N, 0);
+  const int ntiles = (int)((N + sh.R - 1) / sh.R);
+  return tdm_refined_launch(sh, p->t, nullptr, &one, ntiles, p->dev_err, s);
 }
