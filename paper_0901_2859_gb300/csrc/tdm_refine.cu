@@ -15,10 +15,11 @@
 //     x  += solve32(r)
 //   X_i = xh_i + xl_i rounded once to binary64.
 //
-// x is held as a binary32 pair: high words in registers, low words in shared
-// memory.  F is read from global memory for the first solve and again (from
-// L2) for each residual, so shared memory holds no copy of the tile and two
-// CTAs fit on an SM.
+// x is held as x0 + delta: x0, the first solve's binary32 result, in
+// registers; delta, the sum of the corrections, in shared memory, updated with
+// an exact TwoSum whose rounding error is carried to the output.  F is read
+// from global memory for the first solve and again (from L2) for each
+// residual, so shared memory holds no copy of the tile.
 //
 // The residual is formed in row-sum form.  With sigma_i = b_i + a_{i-1} + a_i
 // and the fluxes E_i = a_i (x_{i+1} - x_i),
@@ -112,12 +113,15 @@ __device__ __forceinline__ void forward_pass_g(float (&v)[TT], const float* cf, 
   }
 }
 
-// A5 of a correction solve: back substitution, correction with the separator
-// values, and x += d in pair arithmetic (high words in registers, low words in
-// shared memory at stride R); tracks max|d| and max|x| for the convergence test.
+// A5 of a solve: back substitution and correction with the separator values.
+// The iterate is x = x0 + delta: x0 (registers) is the first solve's result,
+// delta (shared memory, stride R) accumulates the corrections.  A correction d
+// is added to delta with Knuth's TwoSum; its exact rounding error replaces
+// g[i] so that the final output can include it.  Tracks max|d| and max|x| for
+// the convergence test.
 template <int R, int TT, bool FULL, bool SM>
-__device__ __forceinline__ void backward_update(const float (&g)[TT], const float* cf, int nrows, float xL,
-                                                float xR, float (&xh)[TT], float* xlt, float& maxd,
+__device__ __forceinline__ void backward_update(float (&g)[TT], const float* cf, int nrows, float xL, float xR,
+                                                bool first, float (&x0)[TT], float* delta, float& maxd,
                                                 float& maxx) {
   float y = 0.f;
 #pragma unroll
@@ -127,11 +131,16 @@ __device__ __forceinline__ void backward_update(const float (&g)[TT], const floa
       cld4<SM>(cf + i * kNCOEF + 4, cc, invd, phl, phr);
       y = fmaf(-cc, y, g[i]) * invd;
       const float d = fmaf(phr, xR, fmaf(phl, xL, y));
-      const f2pair xn = df_add_f(f2pair{xh[i], xlt[i * R]}, d);
-      xh[i] = xn.h;
-      xlt[i * R] = xn.l;
+      if (first) {
+        x0[i] = d;
+        g[i] = 0.f;
+      } else {
+        const f2pair sd = two_sum_f(delta[i * R], d);
+        delta[i * R] = sd.h;
+        g[i] = sd.l;
+      }
       maxd = fmaxf(maxd, fabsf(d));
-      maxx = fmaxf(maxx, fabsf(xn.h));
+      maxx = fmaxf(maxx, fabsf(x0[i]));
     }
   }
 }
@@ -162,7 +171,7 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   const int bl = tid / R;
   const int cluster_id = blockIdx.x / L.C;
   const int nclusters = gridDim.x / L.C;
-  float* xlt = sxl + (size_t)bl * TT * R + r;   // this thread's low words (valid when bl < m)
+  float* xlt = sxl + (size_t)bl * TT * R + r;   // this thread's delta words (valid when bl < m)
 
   SolveArgs a;   // per-series view used by the shared step-A4 code
   memset(&a, 0, sizeof(a));
@@ -301,8 +310,8 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
         if (b + 1 <= item.M - 1) xR = separator_value<float, R>(s, bl + 1, r);
       }
       float maxd = 0.f, maxx = 0.f;
-      if (nrows == TT) backward_update<R, TT, true, SM>(g, cfb, nrows, xL, xR, xh, xlt, maxd, maxx);
-      else backward_update<R, TT, false, SM>(g, cfb, nrows, xL, xR, xh, xlt, maxd, maxx);
+      if (nrows == TT) backward_update<R, TT, true, SM>(g, cfb, nrows, xL, xR, step == 0, xh, xlt, maxd, maxx);
+      else backward_update<R, TT, false, SM>(g, cfb, nrows, xL, xR, step == 0, xh, xlt, maxd, maxx);
       if (!col_ok) maxd = maxx = 0.f;   // padding columns of a ragged tile do not vote
       if (adaptive && step >= 1) {   // per-CTA, per-column maxima of |d| and |x| for the test
         if (bl < m) { redD[bl * R + r] = maxd; redX[bl * R + r] = maxx; }
@@ -329,7 +338,10 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       double* Xp = item.X + row0 * item.ldX + col;
 #pragma unroll
       for (int i = 0; i < TT; i++)
-        if (i < nrows) st_stream(Xp + (int64_t)i * item.ldX, tdm_f2d(xh[i]) + tdm_f2d(xlt[i * R]));
+        if (i < nrows) {   // x0 + delta + (last rounding error, in g), rounded once
+          const f2pair sx = two_sum_f(xh[i], xlt[i * R]);
+          st_stream(Xp + (int64_t)i * item.ldX, tdm_f2d(sx.h) + tdm_f2d(sx.l + g[i]));
+        }
     }
   }
   // no CTA may leave while a peer can still read its shared memory
@@ -392,15 +404,21 @@ tdm_status launch_shape(const RefShape& sh, const RefLaunch& L, int nitems, cuda
 }  // namespace
 
 // Tile shapes: R right-hand sides per tile, NT threads per CTA, m = NT / R
-// blocks per CTA.  R = 8 with 256 threads lets two CTAs share an SM (n up to
-// 16 * 32 * t rows); R = 4 with 512 threads reaches 4 times further (n up to
-// 65536 for t = 32); R = 16 with 512 threads is selectable for experiments.
+// blocks of t rows per CTA, up to 16 CTAs per cluster.
+//   t = 16: R = 8, 512 threads, two CTAs per SM (64 registers), 1024 rows per
+//           CTA (n <= 16384); R = 4 with 512 threads (2048 rows) or 1024
+//           threads (4096 rows, n <= 65536), coefficients read through L1.
+//   t = 32: R = 8, 256 threads, two CTAs per SM (128 registers, n <= 16384);
+//           R = 4, 512 threads (n <= 65536); R = 16, 512 threads on request.
 bool tdm_refined_shape(int M, int t, RefShape& sh) {
   const char* env = getenv("TDM_REFINE_R");
   const int pref = env ? atoi(env) : 8;
-  const int cand[3][2] = {{pref, pref == 8 ? 256 : 512}, {8, 256}, {4, 512}};
-  for (const auto& cr : cand) {
-    const int R = cr[0], NT = cr[1];
+  struct Cand { int R, NT; bool sm; };
+  const Cand c16[3] = {{8, 512, true}, {4, 512, false}, {4, 1024, false}};
+  const Cand c32[3] = {{pref, pref == 8 ? 256 : 512, pref != 4}, {8, 256, true}, {4, 512, false}};
+  const Cand* cand = t == 16 ? c16 : c32;
+  for (int k = 0; k < 3; k++) {
+    const int R = cand[k].R, NT = cand[k].NT;
     if (R != 4 && R != 8 && R != 16) continue;
     const int m_max = NT / R;
     const int C = (M + m_max - 1) / m_max;
@@ -409,7 +427,7 @@ bool tdm_refined_shape(int M, int t, RefShape& sh) {
     sh.R = R; sh.NT = NT; sh.m = m; sh.C = C;
     sh.threads = ((m * R + 31) / 32) * 32;
     if (sh.threads < 96) sh.threads = 96;
-    sh.sm_coef = R != 4;
+    sh.sm_coef = cand[k].sm;
     sh.smem = refine_smem_bytes(m, t, R, sh.sm_coef);
     if (sh.smem > 227 * 1024) continue;
     return true;
@@ -429,14 +447,14 @@ tdm_status tdm_refined_launch(const RefShape& sh, int t, const RefItem* items, c
   L.m = sh.m;
   L.C = sh.C;
   L.err = err;
-  const int key = sh.R * 10000 + sh.NT * 10 + (t == 16 ? 1 : 0);
+  const int key = sh.R * 100000 + sh.NT * 10 + (t == 16 ? 1 : 0);
   switch (key) {
-    case 8 * 10000 + 256 * 10 + 0: return launch_shape<8, 32, 256, 2, true>(sh, L, nitems, s);
-    case 4 * 10000 + 512 * 10 + 0: return launch_shape<4, 32, 512, 1, false>(sh, L, nitems, s);
-    case 16 * 10000 + 512 * 10 + 0: return launch_shape<16, 32, 512, 1, true>(sh, L, nitems, s);
-    case 8 * 10000 + 256 * 10 + 1: return launch_shape<8, 16, 256, 2, true>(sh, L, nitems, s);
-    case 4 * 10000 + 512 * 10 + 1: return launch_shape<4, 16, 512, 1, false>(sh, L, nitems, s);
-    case 16 * 10000 + 512 * 10 + 1: return launch_shape<16, 16, 512, 1, true>(sh, L, nitems, s);
+    case 8 * 100000 + 256 * 10 + 0: return launch_shape<8, 32, 256, 2, true>(sh, L, nitems, s);
+    case 4 * 100000 + 512 * 10 + 0: return launch_shape<4, 32, 512, 1, false>(sh, L, nitems, s);
+    case 16 * 100000 + 512 * 10 + 0: return launch_shape<16, 32, 512, 1, true>(sh, L, nitems, s);
+    case 8 * 100000 + 512 * 10 + 1: return launch_shape<8, 16, 512, 2, true>(sh, L, nitems, s);
+    case 4 * 100000 + 512 * 10 + 1: return launch_shape<4, 16, 512, 2, false>(sh, L, nitems, s);
+    case 4 * 100000 + 1024 * 10 + 1: return launch_shape<4, 16, 1024, 1, false>(sh, L, nitems, s);
   }
   return TDM_ERR_NOT_IMPLEMENTED;
 }
