@@ -58,7 +58,8 @@ typedef enum {
   TDM_ERR_NO_MEMORY = 4,        /* device allocation failed */
   TDM_ERR_NOT_CONVERGED = 5,    /* refinement did not reach its tolerance within its cap */
   TDM_ERR_TIMEOUT = 6,          /* a bounded device wait gave up */
-  TDM_ERR_NOT_IMPLEMENTED = 7   /* the requested combination is not available */
+  TDM_ERR_NOT_IMPLEMENTED = 7,  /* the requested combination is not available */
+  TDM_ERR_TOO_LARGE = 8         /* the work exceeds a fixed capacity (tdm_solve_batched_noalloc) */
 } tdm_status;
 
 /* Arithmetic of a solve and the dtypes of F and X:
@@ -132,6 +133,36 @@ tdm_status tdm_solve_batched(const tdm_handle* hs, int count,
                              const void* const* F, const int64_t* ldF,
                              void* const* X, const int64_t* ldX, const int64_t* N,
                              tdm_precision prec, void* stream);
+
+/* tdm_solve_batched_noalloc -- tdm_solve_batched with TDM_FP32_REFINED for
+ * callers that must not allocate: the call allocates no device or host memory
+ * (no cudaMalloc, cudaMallocHost, cudaFree).  The paper has no counterpart:
+ * this is a memory-management variant of the batched solve, not a step of the
+ * method.  Callers who cannot allocate: one whose device memory is held by
+ * its own pool (a cudaMalloc could fail although the pool has room); one in a
+ * loop overlapping several streams (allocation and release may synchronize the
+ * device); one passing new F / X pointers every call (tdm_solve_batched keeps
+ * one work list per argument set until a plan is destroyed).
+ *   Arguments as tdm_solve_batched: hs[k], F[k] (binary32), ldF[k], X[k]
+ *   (binary64), ldX[k], N[k]; all plans on one device, same block_rows.
+ * The work list -- one item per tile of right-hand sides, ceil(N[k] / R)
+ * items for series k, R = 4, 8 or 16 by the series' size -- is written into a
+ * fixed device array of TDM_NOALLOC_MAX_TILES items (384 KiB), one per device,
+ * shared by all calls on that device and keeping the last call's items.
+ *   - The first call on a device sets it up (looks up the array's device
+ *     address, loading the library's device code there); make it before any
+ *     stream capture.
+ *   - Calls that overlap on the device (different streams with no ordering
+ *     between them) race on the array: serialize them on one stream.
+ * The note on CUDA graphs at the top of this file does not cover this entry
+ * point.
+ * Errors: as tdm_solve_batched; TDM_ERR_TOO_LARGE when the items of one call
+ * exceed TDM_NOALLOC_MAX_TILES (nothing is enqueued). */
+#define TDM_NOALLOC_MAX_TILES 4096
+tdm_status tdm_solve_batched_noalloc(const tdm_handle* hs, int count,
+                                     const float* const* F, const int64_t* ldF,
+                                     double* const* X, const int64_t* ldX, const int64_t* N,
+                                     void* stream);
 
 /* tdm_solve_backward -- gradients of a scalar loss L through X = A^{-1} F.
  * A is symmetric, so the adjoint system A^T Lambda = W is another solve with

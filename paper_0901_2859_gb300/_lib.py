@@ -11,13 +11,14 @@ TDM_OK = 0
 STATUS_NAMES = {
     0: "TDM_OK", 1: "TDM_ERR_INVALID_ARG", 2: "TDM_ERR_SINGULAR", 3: "TDM_ERR_CUDA",
     4: "TDM_ERR_NO_MEMORY", 5: "TDM_ERR_NOT_CONVERGED", 6: "TDM_ERR_TIMEOUT",
-    7: "TDM_ERR_NOT_IMPLEMENTED",
+    7: "TDM_ERR_NOT_IMPLEMENTED", 8: "TDM_ERR_TOO_LARGE",
 }
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_refined": 2}
 
 # every symbol include/tdm.h declares
-EXPORTS = ("tdm_prepare", "tdm_solve", "tdm_solve_batched", "tdm_solve_backward",
-           "tdm_get_info", "tdm_destroy", "tdm_status_string")
+EXPORTS = ("tdm_prepare", "tdm_solve", "tdm_solve_batched", "tdm_solve_batched_noalloc",
+           "tdm_solve_backward", "tdm_get_info", "tdm_destroy", "tdm_status_string")
+NOALLOC_MAX_TILES = 4096   # TDM_NOALLOC_MAX_TILES
 
 
 class TDMOptions(ctypes.Structure):
@@ -63,6 +64,9 @@ def load(build_if_missing: bool = True):
         lib.tdm_solve.argtypes = [vp, vp, i64, vp, i64, i64, i32, vp]
         lib.tdm_solve_batched.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                                           ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i64), i32, vp]
+        lib.tdm_solve_batched_noalloc.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp),
+                                                  ctypes.POINTER(i64), ctypes.POINTER(vp),
+                                                  ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
         lib.tdm_solve_backward.argtypes = [vp, vp, vp, i64, i64, vp, vp, vp, i32, vp]
         lib.tdm_get_info.argtypes = [vp, ctypes.POINTER(TDMInfo)]
         lib.tdm_destroy.argtypes = [vp]

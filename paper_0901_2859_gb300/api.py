@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import PRECISIONS, TDMError, TDMInfo, TDMOptions, check
 
-__all__ = ["Plan", "prepare", "solve_batched", "TDMSolve", "tdm_solve", "TDMError"]
+__all__ = ["Plan", "prepare", "solve_batched", "solve_batched_noalloc", "TDMSolve", "tdm_solve", "TDMError"]
 
 _OUT_DTYPE = {"fp64": torch.float64, "fp32": torch.float32, "fp32_refined": torch.float64}
 _IN_DTYPE = {"fp64": torch.float64, "fp32": torch.float32, "fp32_refined": torch.float32}
@@ -162,6 +162,31 @@ def solve_batched(plans, Fs, precision: str = "fp32_refined", outs=None):
         st = _lib.load().tdm_solve_batched(hs, count, fp, ldf, xp, ldx, ns, PRECISIONS[precision],
                                            _stream_ptr(dev))
     check(st, "tdm_solve_batched")
+    return outs
+
+
+def solve_batched_noalloc(plans, Fs, outs):
+    """``solve_batched`` (refined) through ``tdm_solve_batched_noalloc``: the
+    library allocates nothing; the caller provides every output."""
+    if not (len(plans) == len(Fs) == len(outs)):
+        raise ValueError("plans, Fs and outs must have the same length")
+    count = len(plans)
+    hs = (ctypes.c_void_p * count)(*[p.handle.value for p in plans])
+    fp = (ctypes.c_void_p * count)()
+    xp = (ctypes.c_void_p * count)()
+    ldf = (ctypes.c_int64 * count)()
+    ldx = (ctypes.c_int64 * count)()
+    ns = (ctypes.c_int64 * count)()
+    for k, (p, F, X) in enumerate(zip(plans, Fs, outs)):
+        ldf[k] = _check_rhs(F, p.n, torch.float32, f"Fs[{k}]")
+        ldx[k] = _check_rhs(X, p.n, torch.float64, f"outs[{k}]")
+        fp[k] = F.data_ptr()
+        xp[k] = X.data_ptr()
+        ns[k] = int(F.shape[1])
+    dev = plans[0].device if count else torch.device("cuda")
+    with torch.cuda.device(dev):
+        st = _lib.load().tdm_solve_batched_noalloc(hs, count, fp, ldf, xp, ldx, ns, _stream_ptr(dev))
+    check(st, "tdm_solve_batched_noalloc")
     return outs
 
 

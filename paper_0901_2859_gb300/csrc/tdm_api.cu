@@ -93,6 +93,12 @@ __global__ void __launch_bounds__(256) k_grad_rows(const T* __restrict__ L, cons
 
 }  // namespace
 
+// argument checks of tdm_solve, for the entry points defined in other files
+tdm_status tdm_validate_solve(const tdm_plan_s* h, const void* F, int64_t ldF, const void* X, int64_t ldX,
+                              int64_t N, tdm_precision prec) {
+  return validate_solve(h, F, ldF, X, ldX, N, prec);
+}
+
 tdm_status tdm_launch_solve(tdm_plan_s* p, const void* F, int64_t ldF, void* X, int64_t ldX,
                             int64_t N, tdm_precision prec, cudaStream_t s) {
   switch (prec) {
@@ -214,6 +220,7 @@ extern "C" const char* tdm_status_string(tdm_status s) {
     case TDM_ERR_NOT_CONVERGED: return "TDM_ERR_NOT_CONVERGED";
     case TDM_ERR_TIMEOUT: return "TDM_ERR_TIMEOUT";
     case TDM_ERR_NOT_IMPLEMENTED: return "TDM_ERR_NOT_IMPLEMENTED";
+    case TDM_ERR_TOO_LARGE: return "TDM_ERR_TOO_LARGE";
   }
   return "TDM_ERR_UNKNOWN";
 }

@@ -56,6 +56,10 @@ def test_host_validation_rejects_bad_arguments(lib):
     assert lib.tdm_solve_batched(None, -1, None, None, None, None, None, 2, None) == 1
     assert lib.tdm_solve_batched(None, 3, None, None, None, None, None, 2, None) == 1
     assert lib.tdm_solve_batched(None, 0, None, None, None, None, None, 2, None) == 0
+    # batched without allocation: negative count, null arrays, empty call
+    assert lib.tdm_solve_batched_noalloc(None, -1, None, None, None, None, None, None) == 1
+    assert lib.tdm_solve_batched_noalloc(None, 2, None, None, None, None, None, None) == 1
+    assert lib.tdm_solve_batched_noalloc(None, 0, None, None, None, None, None, None) == 0
     # destroy(NULL) is accepted
     assert lib.tdm_destroy(None) == 0
 
