@@ -1,0 +1,286 @@
+// tdm_iface_df.cuh -- step A4 (separator values by Theorem 2, eq. theor_2)
+// for the refined solve, in binary32-pair ("double-float") arithmetic and in
+// logarithmic depth.
+//
+// The separator values are x(p_j) = LR_j + LL_j + piR_j in_R + piL_j in_L
+// with the two first-order recurrences inside a CTA of m blocks
+//     LR_0 = 0,  LR_{j+1} = aR_j LR_j + betaR_j        (left to right)
+//     LL_m = 0,  LL_j     = aL_j LL_{j+1} + betaL_j    (right to left)
+// and in_R, in_L the partial sums that enter the CTA from the CTAs to its left
+// and right.  The multipliers aR_j, aL_j (ratios of neighbouring separators'
+// homogeneous solutions, eq. z_vector) depend on the matrix only, so every
+// product of them that the evaluation needs is formed once per series, in
+// binary64, and kept as pairs:
+//   - each recurrence is a Kogge-Stone scan over the 32 lanes of one warp
+//     (K = ceil(m / 32) consecutive blocks per lane, scanned sequentially
+//     first); level l adds to lane i the value of lane i -/+ 2^l times the
+//     product of the multipliers in between;
+//   - the partial sums of the other CTAs are folded in one round: every lane
+//     reads one CTA's total and multiplies it by the product of the
+//     multipliers of the CTAs in between; a shuffle tree adds them up.
+// A binary64 chain costs ~60 cycles per step on GB300 and the multipliers of
+// an ill-conditioned matrix are close to one, which is why the sums are kept
+// in pairs (~2^-46 relative) rather than in binary32.
+#pragma once
+
+#include "tdm_df.cuh"
+#include "tdm_kernel_common.cuh"
+
+namespace tdmk {
+
+// Shared-memory layout of the A4 arrays for tiles of R right-hand sides and at
+// most MM blocks per CTA (byte offsets from the start of the arrays).
+struct IfaceOffsets {
+  size_t beR, beL;   // float [MM][R] beta^R, beta^L of each block
+  size_t lr, ll;     // pair [MM+1][R] LR_j, LL_j
+  size_t aR, aL;     // pair [MM] multipliers
+  size_t cpR, cpL;   // pair [MM] aR from the lane start through j; aL from j through the lane end
+  size_t ksR, ksL;   // pair [5][32] lane-range products: [i - 2^l + 1, i] and [i, i + 2^l - 1]
+  size_t piR, piL;   // pair [MM+1] aR_0 .. aR_{j-1}; aL_j .. aL_{m-1}
+  size_t wR, wL;     // pair [16] fold weights of the CTAs to the left / right
+  size_t xch;        // pair [2 parity][2 dir][R] this CTA's totals, read by the other CTAs
+  size_t in;         // pair [2][R] in_R, in_L
+  size_t tmp;        // double [96] set-up scratch
+  size_t bytes;
+};
+__host__ __device__ constexpr IfaceOffsets iface_offsets(int R, int MM) {
+  IfaceOffsets o{};
+  size_t p = 0;
+  o.beR = p; p += round16(4 * (size_t)MM * R);
+  o.beL = p; p += round16(4 * (size_t)MM * R);
+  o.lr = p; p += round16(8 * (size_t)(MM + 1) * R);
+  o.ll = p; p += round16(8 * (size_t)(MM + 1) * R);
+  o.aR = p; p += round16(8 * (size_t)MM);
+  o.aL = p; p += round16(8 * (size_t)MM);
+  o.cpR = p; p += round16(8 * (size_t)MM);
+  o.cpL = p; p += round16(8 * (size_t)MM);
+  o.ksR = p; p += 8 * 160;
+  o.ksL = p; p += 8 * 160;
+  o.piR = p; p += round16(8 * (size_t)(MM + 1));
+  o.piL = p; p += round16(8 * (size_t)(MM + 1));
+  o.wR = p; p += 8 * 16;
+  o.wL = p; p += 8 * 16;
+  o.xch = p; p += round16(8 * 4 * (size_t)R);
+  o.in = p; p += round16(8 * 2 * (size_t)R);
+  o.tmp = p; p += 8 * 96;
+  o.bytes = p;
+  return o;
+}
+
+// The arrays at compile-time offsets from `base` (16-byte aligned shared
+// memory), so that every access is an immediate offset.
+template <int R, int MM>
+struct IfaceDF {
+  static constexpr IfaceOffsets O = iface_offsets(R, MM);
+  unsigned char* base;
+  __device__ float* beR() const { return reinterpret_cast<float*>(base + O.beR); }
+  __device__ float* beL() const { return reinterpret_cast<float*>(base + O.beL); }
+  __device__ float2* lr() const { return reinterpret_cast<float2*>(base + O.lr); }
+  __device__ float2* ll() const { return reinterpret_cast<float2*>(base + O.ll); }
+  __device__ float2* aR() const { return reinterpret_cast<float2*>(base + O.aR); }
+  __device__ float2* aL() const { return reinterpret_cast<float2*>(base + O.aL); }
+  __device__ float2* cpR() const { return reinterpret_cast<float2*>(base + O.cpR); }
+  __device__ float2* cpL() const { return reinterpret_cast<float2*>(base + O.cpL); }
+  __device__ float2* ksR() const { return reinterpret_cast<float2*>(base + O.ksR); }
+  __device__ float2* ksL() const { return reinterpret_cast<float2*>(base + O.ksL); }
+  __device__ float2* piR() const { return reinterpret_cast<float2*>(base + O.piR); }
+  __device__ float2* piL() const { return reinterpret_cast<float2*>(base + O.piL); }
+  __device__ float2* wR() const { return reinterpret_cast<float2*>(base + O.wR); }
+  __device__ float2* wL() const { return reinterpret_cast<float2*>(base + O.wL); }
+  __device__ float2* xch() const { return reinterpret_cast<float2*>(base + O.xch); }
+  __device__ float2* in() const { return reinterpret_cast<float2*>(base + O.in); }
+  __device__ double* tmp() const { return reinterpret_cast<double*>(base + O.tmp); }
+};
+
+__device__ __forceinline__ float2 df_of(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+__device__ __forceinline__ f2pair fp(float2 v) { return f2pair{v.x, v.y}; }
+__device__ __forceinline__ float2 f2(f2pair v) { return make_float2(v.h, v.l); }
+
+// a * x + b for pairs, renormalised
+__device__ __forceinline__ f2pair df_fma(f2pair a, f2pair x, f2pair b) {
+  const float p = a.h * x.h;
+  float e = fmaf(a.h, x.h, -p);
+  e = fmaf(a.h, x.l, e);
+  e = fmaf(a.l, x.h, e);
+  const f2pair s = two_sum_f(b.h, p);
+  return fast_two_sum_f(s.h, s.l + (e + b.l));
+}
+__device__ __forceinline__ f2pair df_add(f2pair a, f2pair b) {
+  const f2pair s = two_sum_f(a.h, b.h);
+  return fast_two_sum_f(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ f2pair shfl_up_pair(f2pair v, int d) {
+  return f2pair{__shfl_up_sync(0xffffffffu, v.h, d), __shfl_up_sync(0xffffffffu, v.l, d)};
+}
+__device__ __forceinline__ f2pair shfl_down_pair(f2pair v, int d) {
+  return f2pair{__shfl_down_sync(0xffffffffu, v.h, d), __shfl_down_sync(0xffffffffu, v.l, d)};
+}
+__device__ __forceinline__ f2pair shfl_xor_pair(f2pair v, int d) {
+  return f2pair{__shfl_xor_sync(0xffffffffu, v.h, d), __shfl_xor_sync(0xffffffffu, v.l, d)};
+}
+__device__ __forceinline__ float2 ld_cluster_f32x2(const float2* local, unsigned rank) {
+  const unsigned laddr = (unsigned)__cvta_generic_to_shared(local);
+  unsigned raddr;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(laddr), "r"(rank));
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(raddr) : "memory");
+  return v;
+}
+
+// Per-series set-up of every product (binary64, then pairs).  All threads of
+// the CTA call it; it synchronizes the CTA.  rR, rL have M + 2 entries; the
+// multipliers of CTA c are aR_j = rR[c m + j], aL_j = rL[c m + j + 1].
+template <int R, int MM>
+__device__ __forceinline__ void iface_df_setup(const IfaceDF<R, MM>& f, const double* rR, const double* rL, int M,
+                                               int m, int C, unsigned c) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto gR = [&](int q) -> double { return (q >= 0 && q <= M + 1) ? rR[q] : 0.0; };
+  auto gL = [&](int q) -> double { return (q >= 0 && q <= M + 1) ? rL[q] : 0.0; };
+  const int K = (m + 31) / 32, nl = (m + K - 1) / K;
+  const int b0 = (int)c * m;
+  double* AR = f.tmp();        // [32] lane products
+  double* AL = f.tmp() + 32;
+  double* TR = f.tmp() + 64;   // [16] CTA totals
+  double* TL = f.tmp() + 80;
+  for (int u = tid; u < 64 + 2 + 2 * C; u += nt) {
+    if (u < 64) {   // one lane of one direction: multipliers, in-lane products, lane product
+      const int lane = u & 31;
+      double p = 1.0;
+      if (lane < nl) {
+        const int j0 = lane * K, j1 = min(j0 + K, m);
+        if (u < 32) {
+          for (int j = j0; j < j1; j++) { const double a = gR(b0 + j); f.aR()[j] = df_of(a); p *= a; f.cpR()[j] = df_of(p); }
+        } else {
+          for (int j = j1 - 1; j >= j0; j--) { const double a = gL(b0 + j + 1); f.aL()[j] = df_of(a); p *= a; f.cpL()[j] = df_of(p); }
+        }
+      }
+      (u < 32 ? AR : AL)[lane] = p;
+    } else if (u == 64) {   // prefix products from the left
+      double p = 1.0;
+      f.piR()[0] = df_of(1.0);
+      for (int j = 1; j <= m; j++) { p *= gR(b0 + j - 1); f.piR()[j] = df_of(p); }
+    } else if (u == 65) {   // from the right
+      double p = 1.0;
+      f.piL()[m] = df_of(1.0);
+      for (int j = m - 1; j >= 0; j--) { p *= gL(b0 + j + 1); f.piL()[j] = df_of(p); }
+    } else {                // the totals of every CTA of the cluster
+      const int k = u - 66, cc = k % C;
+      double p = 1.0;
+      if (k < C) for (int j = 0; j < m; j++) p *= gR(cc * m + j);
+      else for (int j = 0; j < m; j++) p *= gL(cc * m + j + 1);
+      (k < C ? TR : TL)[cc] = p;
+    }
+  }
+  __syncthreads();
+  for (int u = tid; u < 320 + 32; u += nt) {
+    if (u < 320) {   // scan-level products
+      const bool left = u < 160;
+      const int l = (u % 160) / 32, lane = u % 32, d = 1 << l;
+      double p = 1.0;
+      if (left) {
+        for (int q = lane - d + 1; q <= lane; q++) if (q >= 0) p *= AR[q];
+        f.ksR()[l * 32 + lane] = df_of(p);
+      } else {
+        for (int q = lane; q <= lane + d - 1; q++) if (q < 32) p *= AL[q];
+        f.ksL()[l * 32 + lane] = df_of(p);
+      }
+    } else {         // fold weights
+      const int k = u - 320, cc = k % 16;
+      double p = 0.0;
+      if (k < 16) {
+        if (cc < (int)c) { p = 1.0; for (int q = cc + 1; q < (int)c; q++) p *= TR[q]; }
+        f.wR()[cc] = df_of(p);
+      } else {
+        if (cc > (int)c && cc < C) { p = 1.0; for (int q = (int)c + 1; q < cc; q++) p *= TL[q]; }
+        f.wL()[cc] = df_of(p);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// LR_j, LL_j of this CTA and its totals (into xch[parity]); one warp scans a
+// column in both directions.  The betas must be visible (CTA barrier).
+template <int R, int MM>
+__device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM>& f, int m, int parity) {
+  const int lane = threadIdx.x & 31;
+  const int K = (m + 31) / 32, nl = (m + K - 1) / K;
+  const int j0 = lane * K, j1 = min(j0 + K, m);
+  for (int r = threadIdx.x >> 5; r < R; r += blockDim.x >> 5) {
+    // in-lane sequential parts (stored, then completed with what enters the lane)
+    f2pair accR{0.f, 0.f}, accL{0.f, 0.f};
+    for (int j = j0; j < j1; j++) {
+      accR = df_fma(fp(f.aR()[j]), accR, f2pair{f.beR()[j * R + r], 0.f});
+      if (K > 1) f.lr()[(j + 1) * R + r] = f2(accR);
+    }
+    for (int j = j1 - 1; j >= j0; j--) {
+      accL = df_fma(fp(f.aL()[j]), accL, f2pair{f.beL()[j * R + r], 0.f});
+      if (K > 1) f.ll()[j * R + r] = f2(accL);
+    }
+#pragma unroll
+    for (int l = 0; l < 5; l++) {
+      const int d = 1 << l;
+      const f2pair pR = shfl_up_pair(accR, d);
+      const f2pair pL = shfl_down_pair(accL, d);
+      if (lane >= d && lane < nl) accR = df_fma(fp(f.ksR()[l * 32 + lane]), pR, accR);
+      if (lane + d < nl) accL = df_fma(fp(f.ksL()[l * 32 + lane]), pL, accL);
+    }
+    if (K > 1) {
+      f2pair eR = shfl_up_pair(accR, 1);     // everything left of this lane
+      f2pair eL = shfl_down_pair(accL, 1);   // everything right of it
+      if (lane == 0) eR = f2pair{0.f, 0.f};
+      if (lane + 1 >= nl) eL = f2pair{0.f, 0.f};
+      for (int j = j0; j < j1; j++) {
+        f.lr()[(j + 1) * R + r] = f2(df_fma(fp(f.cpR()[j]), eR, fp(f.lr()[(j + 1) * R + r])));
+        f.ll()[j * R + r] = f2(df_fma(fp(f.cpL()[j]), eL, fp(f.ll()[j * R + r])));
+      }
+    } else if (j0 < m) {   // one block per lane: the scan already holds the values
+      f.lr()[(j0 + 1) * R + r] = f2(accR);
+      f.ll()[j0 * R + r] = f2(accL);
+    }
+    if (lane == 0) {
+      f.lr()[r] = make_float2(0.f, 0.f);
+      f.ll()[m * R + r] = make_float2(0.f, 0.f);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      f.xch()[(parity * 2 + 0) * R + r] = f.lr()[m * R + r];
+      f.xch()[(parity * 2 + 1) * R + r] = f.ll()[r];
+    }
+  }
+}
+
+// in_R, in_L of every column from the other CTAs' totals (after a cluster
+// barrier): one warp per column, lanes 0-15 for the CTAs to the left, 16-31
+// for those to the right.
+template <int R, int MM>
+__device__ __forceinline__ void iface_df_fold(const IfaceDF<R, MM>& f, int C, unsigned c, int parity) {
+  const int lane = threadIdx.x & 31, cc = lane & 15;
+  const bool left = lane < 16;
+  const bool valid = left ? (cc < (int)c) : (cc > (int)c && cc < C);
+  for (int r = threadIdx.x >> 5; r < R; r += blockDim.x >> 5) {
+    f2pair v{0.f, 0.f};
+    if (valid) {
+      const float2 x = ld_cluster_f32x2(f.xch() + (parity * 2 + (left ? 0 : 1)) * R + r, (unsigned)cc);
+      v = df_fma(fp(left ? f.wR()[cc] : f.wL()[cc]), fp(x), f2pair{0.f, 0.f});
+    }
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) v = df_add(v, shfl_xor_pair(v, o));
+    if (lane == 0) f.in()[r] = f2(v);
+    if (lane == 16) f.in()[R + r] = f2(v);
+  }
+}
+
+// x(p_j) for column r, rounded to binary32
+template <int R, int MM>
+__device__ __forceinline__ float iface_df_sep(const IfaceDF<R, MM>& f, int j, int r) {
+  f2pair x = df_add(fp(f.lr()[j * R + r]), fp(f.ll()[j * R + r]));
+  x = df_fma(fp(f.piR()[j]), fp(f.in()[r]), x);
+  x = df_fma(fp(f.piL()[j]), fp(f.in()[R + r]), x);
+  return x.h + x.l;
+}
+
+}  // namespace tdmk

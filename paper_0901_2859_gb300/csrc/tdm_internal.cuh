@@ -79,25 +79,31 @@ static inline bool tdm_aligned(const void* p, uintptr_t a) {
 // Exact binary32 <-> binary64 conversions on the integer pipe.  On GB300 the
 // F2F conversion instructions run at the binary64 rate (~2 per clock per SM),
 // 60x slower than integer logic, so the solve kernels move values between the
-// two formats by rebuilding the bit patterns.  Zero, subnormal, infinite and
-// NaN inputs take the hardware conversion.
+// two formats by rebuilding the bit patterns.  Zeros stay on that path too;
+// subnormal, infinite and NaN inputs call the hardware conversion out of line
+// (a call, so that the conversion is never issued as predicated code).
 // ---------------------------------------------------------------------------
+static __device__ __noinline__ double tdm_f2d_hw(float f) { return (double)f; }
+static __device__ __noinline__ float tdm_d2f_hw(double d) { return (float)d; }
+
 __device__ __forceinline__ double tdm_f2d(float f) {
   const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-  const uint32_t lo = u << 29;
-  return __hiloint2double((int)hi, (int)lo);
+  const uint32_t a = u & 0x7fffffffu;
+  if ((a - 0x00800000u) >= 0x7f000000u && a != 0u) return tdm_f2d_hw(f);   // subnormal, inf, NaN
+  const uint32_t hi = a == 0u ? u : (u & 0x80000000u) | ((a >> 3) + 0x38000000u);
+  return __hiloint2double((int)hi, (int)(u << 29));
 }
 
 // binary64 -> binary32, round to nearest even (values in the normal binary32
-// range; everything else takes the hardware conversion).
+// range and zeros; everything else takes the hardware conversion).
 __device__ __forceinline__ float tdm_d2f(double d) {
   const uint32_t hi = (uint32_t)__double2hiint(d);
   const uint32_t lo = (uint32_t)__double2loint(d);
   const uint32_t e = (hi >> 20) & 0x7ffu;
-  if (e <= 896u || e >= 1151u) return (float)d;
+  if (e <= 896u || e >= 1151u) {
+    if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+    return tdm_d2f_hw(d);
+  }
   uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
   const uint32_t rem = lo & 0x1fffffffu;
   uint32_t bits = (hi & 0x80000000u) | ((e - 896u) << 23) | m;

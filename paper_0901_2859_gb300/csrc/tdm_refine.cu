@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "tdm_df.cuh"
+#include "tdm_iface_df.cuh"
 #include "tdm_kernel_common.cuh"
 #include "tdm_refine.cuh"
 #include "tdm_tma.cuh"
@@ -82,7 +83,7 @@ __device__ __forceinline__ float ld_stream(const float* p) {
   return v;
 }
 __device__ __forceinline__ void st_stream(double* p, double v) {
-  asm volatile("st.global.cs.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+  asm volatile("st.global.cs.f64 [%0], %1;" ::"l"(p), "d"(v));
 }
 __device__ __forceinline__ void ldg4(const float* p, float& x, float& y, float& z, float& w) {
   const float4 v = __ldg(reinterpret_cast<const float4*>(p));
@@ -113,16 +114,59 @@ __device__ __forceinline__ void forward_pass_g(float (&v)[TT], const float* cf, 
   }
 }
 
+// F of one block for one right-hand side (zero outside the system)
+template <int TT, bool FULL>
+__device__ __forceinline__ void load_rhs(float (&g)[TT], const float* Fp, int64_t ldF, bool active, int nrows) {
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < TT; i++) {
+      g[i] = (FULL || i < nrows) ? ld_stream(Fp) : 0.f;
+      Fp += ldF;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < TT; i++) g[i] = 0.f;
+  }
+}
+
+// Residual r = F - A x of the iterate x = x0 + delta over one block, in
+// row-sum form: r_i = F_i - sigma_i x_i + E_{i-1} - E_i with the fluxes
+// E_i = a_i (x_{i+1} - x_i).  g holds F on entry and r on exit.  Ep is the
+// flux into the block's first row; xp is x at the row after the block.
+// FIRST: delta is still zero (first correction), so the differences of x are
+// single TwoSums and sigma x a pair-by-float product.  Rows past n carry zero
+// coefficients, F and x, so they add nothing.
+template <int R, int TT, bool FULL, bool FIRST, bool SM, int RS>
+__device__ __forceinline__ void residual_block(float (&g)[TT], const float (&x0)[TT], const float* delta,
+                                               const float* rsb, f2pair Ep, f2pair xp, int nrows) {
+  f2pair xi{x0[0], FIRST ? 0.f : delta[0]};
+#pragma unroll
+  for (int i = 0; i < TT; i++) {
+    float sh = 0.f, sl = 0.f, ah = 0.f, al = 0.f;
+    if (FULL || i < nrows) cld4<SM>(rsb + i * RS, sh, sl, ah, al);   // kS0, kS1, kA0, kA1
+    const f2pair xn = (i + 1 < TT) ? f2pair{x0[i + 1], FIRST ? 0.f : delta[(i + 1) * R]} : xp;
+    const f2pair E = df_mul(f2pair{ah, al}, FIRST ? two_sum_f(xn.h, -xi.h) : df_diff(xn, xi));
+    const f2pair S = FIRST ? df_mul_f(f2pair{sh, sl}, xi.h) : df_mul(f2pair{sh, sl}, xi);
+    const f2pair w = two_sum_f(Ep.h, -E.h);
+    const f2pair u = two_sum_f(g[i], w.h);
+    const f2pair v = two_sum_f(u.h, -S.h);
+    const float small = ((Ep.l - E.l) - S.l) + (w.l + u.l + v.l);
+    g[i] = v.h + small;
+    Ep = E;
+    xi = xn;
+  }
+}
+
 // A5 of a solve: back substitution and correction with the separator values.
 // The iterate is x = x0 + delta: x0 (registers) is the first solve's result,
-// delta (shared memory, stride R) accumulates the corrections.  A correction d
-// is added to delta with Knuth's TwoSum; its exact rounding error replaces
-// g[i] so that the final output can include it.  Tracks max|d| and max|x| for
-// the convergence test.
-template <int R, int TT, bool FULL, bool SM>
+// delta (shared memory, stride R) accumulates the corrections.
+//   FIRST (the first solve): x0 = d, g = 0.
+//   otherwise: d is added to delta with Knuth's TwoSum; its exact rounding
+//   error replaces g[i], so that the output can include the last one.
+// TRACK: maxd = max |d| over the block (for the convergence test).
+template <int R, int TT, bool FULL, bool SM, bool FIRST, bool TRACK>
 __device__ __forceinline__ void backward_update(float (&g)[TT], const float* cf, int nrows, float xL, float xR,
-                                                bool first, float (&x0)[TT], float* delta, float& maxd,
-                                                float& maxx) {
+                                                float (&x0)[TT], float* delta, float& maxd) {
   float y = 0.f;
 #pragma unroll
   for (int i = TT - 1; i >= 0; i--) {
@@ -131,7 +175,7 @@ __device__ __forceinline__ void backward_update(float (&g)[TT], const float* cf,
       cld4<SM>(cf + i * kNCOEF + 4, cc, invd, phl, phr);
       y = fmaf(-cc, y, g[i]) * invd;
       const float d = fmaf(phr, xR, fmaf(phl, xL, y));
-      if (first) {
+      if (FIRST) {
         x0[i] = d;
         g[i] = 0.f;
       } else {
@@ -139,103 +183,137 @@ __device__ __forceinline__ void backward_update(float (&g)[TT], const float* cf,
         delta[i * R] = sd.h;
         g[i] = sd.l;
       }
-      maxd = fmaxf(maxd, fabsf(d));
-      maxx = fmaxf(maxx, fabsf(x0[i]));
+      if (TRACK) maxd = fmaxf(maxd, fabsf(d));
     }
   }
+}
+
+template <int R, int TT, bool FULL, bool SM>
+__device__ __forceinline__ void backward_any(bool first, bool track, float (&g)[TT], const float* cf, int nrows,
+                                             float xL, float xR, float (&x0)[TT], float* delta, float& maxd) {
+  if (first) backward_update<R, TT, FULL, SM, true, true>(g, cf, nrows, xL, xR, x0, delta, maxd);
+  else if (track) backward_update<R, TT, FULL, SM, false, true>(g, cf, nrows, xL, xR, x0, delta, maxd);
+  else backward_update<R, TT, FULL, SM, false, false>(g, cf, nrows, xL, xR, x0, delta, maxd);
+}
+
+// floats per block of the staged solve coefficients (16 bytes of padding)
+template <int TT>
+constexpr int kCfStride = TT * kNCOEF + 4;
+
+// Shared-memory layout of the refined kernel (byte offsets; the same function
+// sizes the launch on the host).
+struct RefOffsets {
+  size_t delta, edge, red, cvg, coef, res, iface, bytes;
+};
+__host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, bool sm_coef) {
+  const size_t MM = (size_t)(NT / R);
+  RefOffsets o{};
+  size_t p = 0;
+  o.delta = p; p += round16(4 * MM * (TT + 1) * R);
+  o.edge = p; p += round16(4 * 4 * MM * R);
+  o.red = p; p += round16(4 * 2 * MM * R);
+  o.cvg = p; p += round16(4 * 4 * (size_t)R);
+  o.coef = p; if (sm_coef) p += round16(4 * MM * (TT * kNCOEF + 4));
+  o.res = p; if (sm_coef) p += round16(16 * MM * (TT + 1));
+  o.iface = p; p += iface_offsets(R, (int)MM).bytes;
+  o.bytes = p;
+  return o;
 }
 
 template <int R, int TT, int NT, int MINB, bool SM>
 __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float ratio_s;
+  constexpr int MM = NT / R;                               // most blocks a CTA can own
+  constexpr RefOffsets O = refine_offsets(R, TT, NT, SM);
   const int m = L.m;
   const int rows_cta = m * TT;
-  unsigned char* p = smem_raw + smem_align_pad(smem_raw);
-  float* sxl = reinterpret_cast<float*>(p); p += round16((size_t)rows_cta * R * 4);   // [rows_cta][R]
-  float* eFh = reinterpret_cast<float*>(p); p += round16((size_t)4 * m * R * 4);     // edges [4][m][R]
-  float* eFl = eFh + m * R;
-  float* eLh = eFl + m * R;
-  float* eLl = eLh + m * R;
-  float* redD = reinterpret_cast<float*>(p); p += round16((size_t)2 * m * R * 4);    // [m][R]
-  float* redX = redD + m * R;
-  float* cvg = reinterpret_cast<float*>(p); p += round16((size_t)4 * R * 4);         // [2][2][R]
+  // Every array at a compile-time offset of the shared window.  Per-block
+  // arrays carry one padding row (sxl, sres) or 16 bytes (scf) per block: the
+  // 32 / R blocks a warp covers then fall in different banks.
+  float* const sxl = reinterpret_cast<float*>(smem_raw + O.delta);   // [MM][TT+1][R] corrections delta
+  float* const eFh = reinterpret_cast<float*>(smem_raw + O.edge);    // [4][MM][R] block edge values of x
+  float* const eFl = eFh + MM * R;
+  float* const eLh = eFl + MM * R;
+  float* const eLl = eLh + MM * R;
+  float* const redD = reinterpret_cast<float*>(smem_raw + O.red);    // [2][MM][R] per-block maxima
+  float* const redX = redD + MM * R;
+  float* const cvg = reinterpret_cast<float*>(smem_raw + O.cvg);     // [2][2][R] per-CTA maxima, read remotely
   // SM: the CTA's coefficient rows, reloaded when the series changes
-  float* scf = reinterpret_cast<float*>(p); if (SM) p += round16((size_t)rows_cta * kNCOEF * 4);   // [rows][8]
-  float* sres = reinterpret_cast<float*>(p); if (SM) p += round16((size_t)(rows_cta + 1) * 4 * 4);  // [rows+1][4]
-  const Smem s = carve(p, m, R, 4);
-
+  float* const scf = reinterpret_cast<float*>(smem_raw + O.coef);    // [MM][TT*8+4]
+  float* const sres = reinterpret_cast<float*>(smem_raw + O.res);    // [MM][TT+1][4]
+  const IfaceDF<R, MM> f{smem_raw + O.iface};
   const unsigned c = cluster_rank();
   const int tid = threadIdx.x;
   const int r = tid % R;
   const int bl = tid / R;
   const int cluster_id = blockIdx.x / L.C;
   const int nclusters = gridDim.x / L.C;
-  float* xlt = sxl + (size_t)bl * TT * R + r;   // this thread's delta words (valid when bl < m)
+  float* xlt = sxl + (size_t)bl * (TT + 1) * R + r;   // this thread's delta words (valid when bl < m)
 
-  SolveArgs a;   // per-series view used by the shared step-A4 code
-  memset(&a, 0, sizeof(a));
-  a.m = m;
-  a.C = L.C;
-  a.err = L.err;
   int cur_series = -1;
   int parity = 0;
 
   for (int it = cluster_id; it < L.nitems; it += nclusters) {
-    const RefItem& item = L.single ? L.one : L.items[it];
-    const int tile = L.single ? it : item.tile;
-    if (item.series != cur_series) {   // new series: ratios and prefix products
+    // fields of the current item, read where they are used (kernel parameter
+    // or work list; no address of the parameter is taken)
+#define ITEM(f) (L.single ? L.one.f : L.items[it].f)
+    const int tile = L.single ? it : L.items[it].tile;
+    if (ITEM(series) != cur_series) {   // new series: ratios and prefix products
       __syncthreads();
-      a.M = item.M;
-      a.n = item.n;
-      a.rR = item.rR;
-      a.rL = item.rL;
-      setup_ratios(a, s, c);
-      if constexpr (SM) {
+      iface_df_setup(f, ITEM(rR), ITEM(rL), ITEM(M), m, L.C, c);
+      if constexpr (SM) {   // rows past n are staged as zeros
         const int64_t cta_row0 = (int64_t)c * rows_cta;
         for (int k = tid; k < rows_cta * kNCOEF / 4; k += blockDim.x) {
-          const int64_t row = cta_row0 + (k * 4) / kNCOEF;
+          const int rr = (k * 4) / kNCOEF;   // row within the CTA
+          const int64_t row = cta_row0 + rr;
           float x = 0.f, y = 0.f, z = 0.f, w = 0.f;
-          if (row < item.n) ldg4(item.coef + cta_row0 * kNCOEF + (int64_t)k * 4, x, y, z, w);
-          float* d = scf + (size_t)k * 4;
+          if (row < ITEM(n)) ldg4(ITEM(coef) + cta_row0 * kNCOEF + (int64_t)k * 4, x, y, z, w);
+          float* d = scf + (size_t)(rr / TT) * kCfStride<TT> + (size_t)(rr % TT) * kNCOEF + (k * 4) % kNCOEF;
           d[0] = x; d[1] = y; d[2] = z; d[3] = w;
         }
-        for (int k = tid; k <= rows_cta; k += blockDim.x) {   // rows cta_row0-1 .. cta_row0+rows_cta-1
-          const int64_t row = cta_row0 - 1 + k;
+        for (int k = tid; k < m * (TT + 1); k += blockDim.x) {   // block j: rows j*TT-1 .. j*TT+TT-1
+          const int64_t row = cta_row0 + (int64_t)(k / (TT + 1)) * TT + (k % (TT + 1)) - 1;
           float x = 0.f, y = 0.f, z = 0.f, w = 0.f;
-          if (row >= 0 && row < item.n) ldg4(item.res + row * kNRES, x, y, z, w);   // kS0, kS1, kA0, kA1
+          if (row >= 0 && row < ITEM(n)) ldg4(ITEM(res) + row * kNRES, x, y, z, w);   // kS0, kS1, kA0, kA1
           float* d = sres + (size_t)k * 4;
           d[0] = x; d[1] = y; d[2] = z; d[3] = w;
         }
       }
       __syncthreads();
-      cur_series = item.series;
+      cur_series = ITEM(series);
     }
-    const int n = item.n;
+    const int n = ITEM(n);
     const int b = (int)c * m + bl;
-    const bool blk_ok = (bl < m) && (b < item.M);
+    const bool blk_ok = (bl < m) && (b < ITEM(M));
     const int64_t row0 = (int64_t)b * TT;
     const int nrows = blk_ok ? (int)((n - row0) < TT ? (n - row0) : TT) : 0;
     const int64_t col = (int64_t)tile * R + r;
-    const bool col_ok = col < item.N;
+    const bool col_ok = col < ITEM(N);
     const bool active = nrows > 0 && col_ok;   // this thread's rows and column exist
-    const float* Fp = item.F + row0 * item.ldF + col;
-    // this block's coefficient rows (rsb[-1] is the row before the block)
-    const float* cfb = SM ? scf + (size_t)bl * TT * kNCOEF : item.coef + row0 * kNCOEF;
-    const float* rsb = SM ? sres + (size_t)(bl * TT + 1) * 4 : item.res + row0 * kNRES;
+    const bool full_rows = nrows == TT;
+    // Arithmetic over all TT rows: with staged coefficients the rows past n
+    // are zeros (F, x and every coefficient), so only F and X need guards.
+    const bool full = SM ? (bl < m) : full_rows;
+    const float* Fp = ITEM(F) + row0 * ITEM(ldF) + col;
+    // this block's coefficient rows (rsb[-RS] is the row before the block)
+    const float* cfb = SM ? scf + (size_t)bl * kCfStride<TT> : ITEM(coef) + row0 * kNCOEF;
+    const float* rsb = SM ? sres + (size_t)(bl * (TT + 1) + 1) * 4 : ITEM(res) + row0 * kNRES;
     constexpr int RS = SM ? 4 : kNRES;   // stride of the residual coefficient rows
-    const bool adaptive = item.steps <= 0;
-    const int cap = adaptive ? 4 : item.steps;
+    const bool adaptive = ITEM(steps) <= 0;
+    const int cap = adaptive ? 4 : ITEM(steps);
 
     float xh[TT], g[TT];
 #pragma unroll
     for (int i = 0; i < TT; i++) {
       xh[i] = 0.f;
       if (bl < m) xlt[i * R] = 0.f;
-      g[i] = (active && i < nrows) ? ld_stream(Fp + (int64_t)i * item.ldF) : 0.f;
     }
+    if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
+    else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
 
     float ratio_prev = 1.f;
+    float maxx = 0.f;   // max |x0| of this thread's rows (the first solve)
     int cpar = 0;
     for (int step = 0;; step++) {
       if (step > 0) {
@@ -254,8 +332,8 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
           if (stop) break;
         }
         if (bl < m) {
-#pragma unroll
-          for (int i = 0; i < TT; i++) g[i] = (active && i < nrows) ? ld_stream(Fp + (int64_t)i * item.ldF) : 0.f;
+          if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
+          else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
           f2pair xm{0.f, 0.f}, xp{0.f, 0.f};   // x at rows row0-1 and row0+TT
           if (bl > 0) {
             xm = f2pair{eLh[(bl - 1) * R + r], eLl[(bl - 1) * R + r]};
@@ -271,49 +349,46 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
             // flux into the first row: E_{row0-1} = a_{row0-1} (x_row0 - x_{row0-1})
             float a_h = 0.f, a_l = 0.f;
             if (row0 > 0) { a_h = rsb[-RS + kA0]; a_l = rsb[-RS + kA1]; }
-            f2pair xi{xh[0], xlt[0]};
-            f2pair Ep = df_mul(f2pair{a_h, a_l}, df_diff(xi, xm));
-#pragma unroll
-            for (int i = 0; i < TT; i++) {
-              // rows beyond n carry zero coefficients and zero iterate, so they add nothing
-              float sh = 0.f, sl = 0.f, ah = 0.f, al = 0.f;
-              if (i < nrows) cld4<SM>(rsb + i * RS, sh, sl, ah, al);   // kS0, kS1, kA0, kA1
-              const f2pair xn = (i + 1 < TT) ? f2pair{xh[i + 1], xlt[(i + 1) * R]} : xp;
-              const f2pair E = df_mul(f2pair{ah, al}, df_diff(xn, xi));
-              const f2pair S = df_mul(f2pair{sh, sl}, xi);
-              const float Fi = g[i];
-              const f2pair w = two_sum_f(Ep.h, -E.h);
-              const f2pair u = two_sum_f(Fi, w.h);
-              const f2pair v = two_sum_f(u.h, -S.h);
-              const float small = ((Ep.l - E.l) - S.l) + (w.l + u.l + v.l);
-              g[i] = v.h + small;
-              Ep = E;
-              xi = xn;
+            const f2pair xi{xh[0], xlt[0]};
+            if (step == 1) {   // delta is still zero
+              const f2pair Ep = df_mul(f2pair{a_h, a_l}, two_sum_f(xi.h, -xm.h));
+              if (full) residual_block<R, TT, true, true, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
+              else residual_block<R, TT, false, true, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
+            } else {
+              const f2pair Ep = df_mul(f2pair{a_h, a_l}, df_diff(xi, xm));
+              if (full) residual_block<R, TT, true, false, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
+              else residual_block<R, TT, false, false, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
             }
           }
         }
       }
       // ---- binary32 dichotomy solve of g (A2-A5) ---------------------------------
       float bR = 0.f, bL = 0.f;
-      if (nrows == TT) forward_pass_g<TT, true, SM>(g, cfb, nrows, bR, bL);
+      if (full) forward_pass_g<TT, true, SM>(g, cfb, nrows, bR, bL);
       else forward_pass_g<TT, false, SM>(g, cfb, nrows, bR, bL);
       if (bl < m) {
-        s.betaR[bl * R + r] = tdm_f2d(bR);
-        s.betaL[bl * R + r] = tdm_f2d(bL);
+        f.beR()[bl * R + r] = bR;
+        f.beL()[bl * R + r] = bL;
       }
       __syncthreads();
-      separator_partials<float, R>(a, s, c, parity);
+      iface_df_scan<R>(f, m, parity);
+      cluster_barrier();
+      iface_df_fold<R>(f, L.C, c, parity);
+      __syncthreads();
       parity ^= 1;
       float xL = 0.f, xR = 0.f;
       if (blk_ok) {
-        if (b >= 1) xL = separator_value<float, R>(s, bl, r);
-        if (b + 1 <= item.M - 1) xR = separator_value<float, R>(s, bl + 1, r);
+        if (b >= 1) xL = iface_df_sep<R>(f, bl, r);
+        if (b + 1 <= ITEM(M) - 1) xR = iface_df_sep<R>(f, bl + 1, r);
       }
-      float maxd = 0.f, maxx = 0.f;
-      if (nrows == TT) backward_update<R, TT, true, SM>(g, cfb, nrows, xL, xR, step == 0, xh, xlt, maxd, maxx);
-      else backward_update<R, TT, false, SM>(g, cfb, nrows, xL, xR, step == 0, xh, xlt, maxd, maxx);
-      if (!col_ok) maxd = maxx = 0.f;   // padding columns of a ragged tile do not vote
-      if (adaptive && step >= 1) {   // per-CTA, per-column maxima of |d| and |x| for the test
+      float maxd = 0.f;
+      const bool first = step == 0;
+      if (full) backward_any<R, TT, true, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
+      else backward_any<R, TT, false, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
+      if (!col_ok) maxd = 0.f;   // padding columns of a ragged tile do not vote
+      if (first) {
+        maxx = maxd;
+      } else if (adaptive) {   // per-CTA, per-column maxima of |d| and |x0| for the test
         if (bl < m) { redD[bl * R + r] = maxd; redX[bl * R + r] = maxx; }
         __syncthreads();
         if (tid < R) {
@@ -333,30 +408,23 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
         break;
       }
     }
-    // ---- X = xh + xl rounded once to binary64 -------------------------------------
+    // ---- X = x0 + delta + (last rounding error, in g), rounded once to binary64 ----
     if (active) {
-      double* Xp = item.X + row0 * item.ldX + col;
+      const int64_t ldX = ITEM(ldX);
+      double* Xp = ITEM(X) + row0 * ldX + col;
 #pragma unroll
-      for (int i = 0; i < TT; i++)
-        if (i < nrows) {   // x0 + delta + (last rounding error, in g), rounded once
+      for (int i = 0; i < TT; i++) {
+        if (full_rows || i < nrows) {
           const f2pair sx = two_sum_f(xh[i], xlt[i * R]);
-          st_stream(Xp + (int64_t)i * item.ldX, tdm_f2d(sx.h) + tdm_f2d(sx.l + g[i]));
+          st_stream(Xp, tdm_f2d(sx.h) + tdm_f2d(sx.l + g[i]));
         }
+        Xp += ldX;
+      }
     }
   }
+#undef ITEM
   // no CTA may leave while a peer can still read its shared memory
   cluster_barrier();
-}
-
-// shared memory of one CTA (after 128-byte alignment)
-size_t refine_smem_bytes(int m, int t, int R, bool sm_coef) {
-  const int rows = m * t;
-  return 128 + round16((size_t)rows * R * 4)   // low words of the iterate
-         + (sm_coef ? round16((size_t)rows * kNCOEF * 4) + round16((size_t)(rows + 1) * 16) : 0)
-         + round16((size_t)4 * m * R * 4)      // block edge values of x (first/last row, hi/lo)
-         + round16((size_t)2 * m * R * 4)      // per-block convergence maxima
-         + round16((size_t)4 * R * 4)          // per-CTA maxima, 2 parities, read remotely
-         + smem_bytes(m, t, R, 4, false) - 128 - coef_bytes(m, t, 4);
 }
 
 template <int R, int TT, int NT, int MINB, bool SM>
@@ -428,7 +496,7 @@ bool tdm_refined_shape(int M, int t, RefShape& sh) {
     sh.threads = ((m * R + 31) / 32) * 32;
     if (sh.threads < 96) sh.threads = 96;
     sh.sm_coef = cand[k].sm;
-    sh.smem = refine_smem_bytes(m, t, R, sh.sm_coef);
+    sh.smem = refine_offsets(R, t, NT, sh.sm_coef).bytes;
     if (sh.smem > 227 * 1024) continue;
     return true;
   }
