@@ -206,19 +206,20 @@ __device__ __forceinline__ void iface_df_setup(const IfaceDF<R, MM>& f, const do
 // column in both directions.  The betas must be visible (CTA barrier).
 template <int R, int MM>
 __device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM>& f, int m, int parity) {
+  constexpr int KMAX = (MM + 31) / 32;   // most blocks per lane (1: every lane holds one block)
   const int lane = threadIdx.x & 31;
-  const int K = (m + 31) / 32, nl = (m + K - 1) / K;
+  const int K = KMAX == 1 ? 1 : (m + 31) / 32, nl = (m + K - 1) / K;
   const int j0 = lane * K, j1 = min(j0 + K, m);
   for (int r = threadIdx.x >> 5; r < R; r += blockDim.x >> 5) {
     // in-lane sequential parts (stored, then completed with what enters the lane)
     f2pair accR{0.f, 0.f}, accL{0.f, 0.f};
     for (int j = j0; j < j1; j++) {
       accR = df_fma(fp(f.aR()[j]), accR, f2pair{f.beR()[j * R + r], 0.f});
-      if (K > 1) f.lr()[(j + 1) * R + r] = f2(accR);
+      if (KMAX > 1 && K > 1) f.lr()[(j + 1) * R + r] = f2(accR);
     }
     for (int j = j1 - 1; j >= j0; j--) {
       accL = df_fma(fp(f.aL()[j]), accL, f2pair{f.beL()[j * R + r], 0.f});
-      if (K > 1) f.ll()[j * R + r] = f2(accL);
+      if (KMAX > 1 && K > 1) f.ll()[j * R + r] = f2(accL);
     }
 #pragma unroll
     for (int l = 0; l < 5; l++) {
@@ -228,7 +229,7 @@ __device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM>& f, int m, in
       if (lane >= d && lane < nl) accR = df_fma(fp(f.ksR()[l * 32 + lane]), pR, accR);
       if (lane + d < nl) accL = df_fma(fp(f.ksL()[l * 32 + lane]), pL, accL);
     }
-    if (K > 1) {
+    if (KMAX > 1 && K > 1) {
       f2pair eR = shfl_up_pair(accR, 1);     // everything left of this lane
       f2pair eL = shfl_down_pair(accL, 1);   // everything right of it
       if (lane == 0) eR = f2pair{0.f, 0.f};

@@ -203,7 +203,7 @@ constexpr int kCfStride = TT * kNCOEF + 4;
 // Shared-memory layout of the refined kernel (byte offsets; the same function
 // sizes the launch on the host).
 struct RefOffsets {
-  size_t delta, edge, red, cvg, coef, res, iface, bytes;
+  size_t delta, edge, red, cvg, coef, res, pad, iface, bytes;
 };
 __host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, bool sm_coef) {
   const size_t MM = (size_t)(NT / R);
@@ -215,6 +215,7 @@ __host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, b
   o.cvg = p; p += round16(4 * 4 * (size_t)R);
   o.coef = p; if (sm_coef) p += round16(4 * MM * (TT * kNCOEF + 4));
   o.res = p; if (sm_coef) p += round16(16 * MM * (TT + 1));
+  o.pad = p; if (sm_coef) p += round16(4 * (size_t)(TT + 1) * R);   // delta words of threads past the blocks
   o.iface = p; p += iface_offsets(R, (int)MM).bytes;
   o.bytes = p;
   return o;
@@ -249,7 +250,13 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   const int bl = tid / R;
   const int cluster_id = blockIdx.x / L.C;
   const int nclusters = gridDim.x / L.C;
-  float* xlt = sxl + (size_t)bl * (TT + 1) * R + r;   // this thread's delta words (valid when bl < m)
+  // Threads past the CTA's blocks (bl >= m) only round the CTA up to whole
+  // warps.  With staged coefficients they run the same full-block code on block
+  // 0's coefficients and a scratch delta block, so that no per-row guard is
+  // compiled in; every result they produce is discarded.
+  const bool pad_thread = bl >= m;
+  float* xlt = (SM && pad_thread) ? reinterpret_cast<float*>(smem_raw + O.pad) + r
+                                  : sxl + (size_t)bl * (TT + 1) * R + r;   // this thread's delta words
 
   int cur_series = -1;
   int parity = 0;
@@ -294,11 +301,12 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
     const bool full_rows = nrows == TT;
     // Arithmetic over all TT rows: with staged coefficients the rows past n
     // are zeros (F, x and every coefficient), so only F and X need guards.
-    const bool full = SM ? (bl < m) : full_rows;
+    const bool full = full_rows;   // (staged coefficients: the full-block code runs always)
+    const int blc = (SM && pad_thread) ? 0 : bl;
     const float* Fp = ITEM(F) + row0 * ITEM(ldF) + col;
     // this block's coefficient rows (rsb[-RS] is the row before the block)
-    const float* cfb = SM ? scf + (size_t)bl * kCfStride<TT> : ITEM(coef) + row0 * kNCOEF;
-    const float* rsb = SM ? sres + (size_t)(bl * (TT + 1) + 1) * 4 : ITEM(res) + row0 * kNRES;
+    const float* cfb = SM ? scf + (size_t)blc * kCfStride<TT> : ITEM(coef) + row0 * kNCOEF;
+    const float* rsb = SM ? sres + (size_t)(blc * (TT + 1) + 1) * 4 : ITEM(res) + row0 * kNRES;
     constexpr int RS = SM ? 4 : kNRES;   // stride of the residual coefficient rows
     const bool adaptive = ITEM(steps) <= 0;
     const int cap = adaptive ? 4 : ITEM(steps);
@@ -307,7 +315,7 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
 #pragma unroll
     for (int i = 0; i < TT; i++) {
       xh[i] = 0.f;
-      if (bl < m) xlt[i * R] = 0.f;
+      if (SM || bl < m) xlt[i * R] = 0.f;
     }
     if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
     else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
@@ -352,20 +360,20 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
             const f2pair xi{xh[0], xlt[0]};
             if (step == 1) {   // delta is still zero
               const f2pair Ep = df_mul(f2pair{a_h, a_l}, two_sum_f(xi.h, -xm.h));
-              if (full) residual_block<R, TT, true, true, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
-              else residual_block<R, TT, false, true, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
+              if (SM || full) residual_block<R, TT, true, true, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
+              else residual_block<R, TT, SM, true, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
             } else {
               const f2pair Ep = df_mul(f2pair{a_h, a_l}, df_diff(xi, xm));
-              if (full) residual_block<R, TT, true, false, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
-              else residual_block<R, TT, false, false, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
+              if (SM || full) residual_block<R, TT, true, false, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
+              else residual_block<R, TT, SM, false, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
             }
           }
         }
       }
       // ---- binary32 dichotomy solve of g (A2-A5) ---------------------------------
       float bR = 0.f, bL = 0.f;
-      if (full) forward_pass_g<TT, true, SM>(g, cfb, nrows, bR, bL);
-      else forward_pass_g<TT, false, SM>(g, cfb, nrows, bR, bL);
+      if (SM || full) forward_pass_g<TT, true, SM>(g, cfb, nrows, bR, bL);
+      else forward_pass_g<TT, SM, SM>(g, cfb, nrows, bR, bL);
       if (bl < m) {
         f.beR()[bl * R + r] = bR;
         f.beL()[bl * R + r] = bL;
@@ -383,8 +391,8 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       }
       float maxd = 0.f;
       const bool first = step == 0;
-      if (full) backward_any<R, TT, true, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
-      else backward_any<R, TT, false, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
+      if (SM || full) backward_any<R, TT, true, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
+      else backward_any<R, TT, SM, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
       if (!col_ok) maxd = 0.f;   // padding columns of a ragged tile do not vote
       if (first) {
         maxx = maxd;
