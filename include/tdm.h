@@ -76,9 +76,9 @@ typedef struct {
   int block_rows;    /* rows per block (the paper's subvector size); 0 = automatic (32).
                         Allowed: 16 or 32. */
   int refine_steps;  /* TDM_FP32_REFINED corrections: k in 1..4 runs exactly k; 0 (automatic)
-                        stops once the estimated relative error is below 1e-12: max|d_1|/max|x|
-                        after the first correction, max|d_k|^2 / (max|x| max|d_{k-1}|) after
-                        later ones; at most 4 corrections (device_error 2 otherwise) */
+                        makes at least two, then stops once the estimated relative error
+                        max|d_k|^2 / (max|x| max|d_{k-1}|) of the last correction is below
+                        1e-12; at most 4 corrections (device_error 2 otherwise) */
   int flags;         /* reserved, must be 0 */
   int reserved;
 } tdm_options;

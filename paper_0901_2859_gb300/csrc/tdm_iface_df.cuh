@@ -31,8 +31,8 @@ namespace tdmk {
 // Shared-memory layout of the A4 arrays for tiles of R right-hand sides and at
 // most MM blocks per CTA (byte offsets from the start of the arrays).
 struct IfaceOffsets {
-  size_t beR, beL;   // float [MM][R] beta^R, beta^L of each block
-  size_t lr, ll;     // pair [MM+1][R] LR_j, LL_j
+  size_t beR, beL;   // float [MM][R+1] beta^R, beta^L of each block (one padding column)
+  size_t lr, ll;     // pair [MM+1][R+1] LR_j, LL_j
   size_t aR, aL;     // pair [MM] multipliers
   size_t cpR, cpL;   // pair [MM] aR from the lane start through j; aL from j through the lane end
   size_t ksR, ksL;   // pair [5][32] lane-range products: [i - 2^l + 1, i] and [i, i + 2^l - 1]
@@ -46,10 +46,10 @@ struct IfaceOffsets {
 __host__ __device__ constexpr IfaceOffsets iface_offsets(int R, int MM) {
   IfaceOffsets o{};
   size_t p = 0;
-  o.beR = p; p += round16(4 * (size_t)MM * R);
-  o.beL = p; p += round16(4 * (size_t)MM * R);
-  o.lr = p; p += round16(8 * (size_t)(MM + 1) * R);
-  o.ll = p; p += round16(8 * (size_t)(MM + 1) * R);
+  o.beR = p; p += round16(4 * (size_t)MM * (R + 1));
+  o.beL = p; p += round16(4 * (size_t)MM * (R + 1));
+  o.lr = p; p += round16(8 * (size_t)(MM + 1) * (R + 1));
+  o.ll = p; p += round16(8 * (size_t)(MM + 1) * (R + 1));
   o.aR = p; p += round16(8 * (size_t)MM);
   o.aL = p; p += round16(8 * (size_t)MM);
   o.cpR = p; p += round16(8 * (size_t)MM);
@@ -72,6 +72,10 @@ __host__ __device__ constexpr IfaceOffsets iface_offsets(int R, int MM) {
 template <int R, int MM>
 struct IfaceDF {
   static constexpr IfaceOffsets O = iface_offsets(R, MM);
+  // Row stride of beR, beL, lr, ll: the scan reads them down a column (lane =
+  // block), the blocks write and read them along a row; one padding entry per
+  // row keeps both directions free of bank conflicts.
+  static constexpr int kRP = R + 1;
   unsigned char* base;
   __device__ float* beR() const { return reinterpret_cast<float*>(base + O.beR); }
   __device__ float* beL() const { return reinterpret_cast<float*>(base + O.beL); }
@@ -121,6 +125,40 @@ __device__ __forceinline__ f2pair shfl_down_pair(f2pair v, int d) {
 __device__ __forceinline__ f2pair shfl_xor_pair(f2pair v, int d) {
   return f2pair{__shfl_xor_sync(0xffffffffu, v.h, d), __shfl_xor_sync(0xffffffffu, v.l, d)};
 }
+// The scan, fold and separator evaluation below run in pairs (PAIR = true,
+// ~2^-46 relative) or in plain binary32 on the leading words (PAIR = false:
+// the products are the same, the sums are rounded to binary32 at every step).
+template <bool PAIR>
+__device__ __forceinline__ f2pair mfma(f2pair a, f2pair x, f2pair b) {
+  if constexpr (PAIR) return df_fma(a, x, b);
+  else return f2pair{fmaf(a.h, x.h, b.h), 0.f};
+}
+template <bool PAIR>
+__device__ __forceinline__ f2pair madd(f2pair a, f2pair b) {
+  if constexpr (PAIR) return df_add(a, b);
+  else return f2pair{a.h + b.h, 0.f};
+}
+template <bool PAIR>
+__device__ __forceinline__ f2pair mshfl_up(f2pair v, int d) {
+  if constexpr (PAIR) return shfl_up_pair(v, d);
+  else return f2pair{__shfl_up_sync(0xffffffffu, v.h, d), 0.f};
+}
+template <bool PAIR>
+__device__ __forceinline__ f2pair mshfl_down(f2pair v, int d) {
+  if constexpr (PAIR) return shfl_down_pair(v, d);
+  else return f2pair{__shfl_down_sync(0xffffffffu, v.h, d), 0.f};
+}
+template <bool PAIR>
+__device__ __forceinline__ f2pair mshfl_xor(f2pair v, int d) {
+  if constexpr (PAIR) return shfl_xor_pair(v, d);
+  else return f2pair{__shfl_xor_sync(0xffffffffu, v.h, d), 0.f};
+}
+template <bool PAIR>
+__device__ __forceinline__ f2pair mld(const float2* p) {
+  if constexpr (PAIR) return fp(*p);
+  else return f2pair{*reinterpret_cast<const float*>(p), 0.f};
+}
+
 __device__ __forceinline__ float2 ld_cluster_f32x2(const float2* local, unsigned rank) {
   const unsigned laddr = (unsigned)__cvta_generic_to_shared(local);
   unsigned raddr;
@@ -204,8 +242,9 @@ __device__ __forceinline__ void iface_df_setup(const IfaceDF<R, MM>& f, const do
 
 // LR_j, LL_j of this CTA and its totals (into xch[parity]); one warp scans a
 // column in both directions.  The betas must be visible (CTA barrier).
-template <int R, int MM>
+template <int R, int MM, bool PAIR = true>
 __device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM>& f, int m, int parity) {
+  constexpr int RP = IfaceDF<R, MM>::kRP;
   constexpr int KMAX = (MM + 31) / 32;   // most blocks per lane (1: every lane holds one block)
   const int lane = threadIdx.x & 31;
   const int K = KMAX == 1 ? 1 : (m + 31) / 32, nl = (m + K - 1) / K;
@@ -214,41 +253,41 @@ __device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM>& f, int m, in
     // in-lane sequential parts (stored, then completed with what enters the lane)
     f2pair accR{0.f, 0.f}, accL{0.f, 0.f};
     for (int j = j0; j < j1; j++) {
-      accR = df_fma(fp(f.aR()[j]), accR, f2pair{f.beR()[j * R + r], 0.f});
-      if (KMAX > 1 && K > 1) f.lr()[(j + 1) * R + r] = f2(accR);
+      accR = mfma<PAIR>(mld<PAIR>(&f.aR()[j]), accR, f2pair{f.beR()[j * RP + r], 0.f});
+      if (KMAX > 1 && K > 1) f.lr()[(j + 1) * RP + r] = f2(accR);
     }
     for (int j = j1 - 1; j >= j0; j--) {
-      accL = df_fma(fp(f.aL()[j]), accL, f2pair{f.beL()[j * R + r], 0.f});
-      if (KMAX > 1 && K > 1) f.ll()[j * R + r] = f2(accL);
+      accL = mfma<PAIR>(mld<PAIR>(&f.aL()[j]), accL, f2pair{f.beL()[j * RP + r], 0.f});
+      if (KMAX > 1 && K > 1) f.ll()[j * RP + r] = f2(accL);
     }
 #pragma unroll
     for (int l = 0; l < 5; l++) {
       const int d = 1 << l;
-      const f2pair pR = shfl_up_pair(accR, d);
-      const f2pair pL = shfl_down_pair(accL, d);
-      if (lane >= d && lane < nl) accR = df_fma(fp(f.ksR()[l * 32 + lane]), pR, accR);
-      if (lane + d < nl) accL = df_fma(fp(f.ksL()[l * 32 + lane]), pL, accL);
+      const f2pair pR = mshfl_up<PAIR>(accR, d);
+      const f2pair pL = mshfl_down<PAIR>(accL, d);
+      if (lane >= d && lane < nl) accR = mfma<PAIR>(mld<PAIR>(&f.ksR()[l * 32 + lane]), pR, accR);
+      if (lane + d < nl) accL = mfma<PAIR>(mld<PAIR>(&f.ksL()[l * 32 + lane]), pL, accL);
     }
     if (KMAX > 1 && K > 1) {
-      f2pair eR = shfl_up_pair(accR, 1);     // everything left of this lane
-      f2pair eL = shfl_down_pair(accL, 1);   // everything right of it
+      f2pair eR = mshfl_up<PAIR>(accR, 1);     // everything left of this lane
+      f2pair eL = mshfl_down<PAIR>(accL, 1);   // everything right of it
       if (lane == 0) eR = f2pair{0.f, 0.f};
       if (lane + 1 >= nl) eL = f2pair{0.f, 0.f};
       for (int j = j0; j < j1; j++) {
-        f.lr()[(j + 1) * R + r] = f2(df_fma(fp(f.cpR()[j]), eR, fp(f.lr()[(j + 1) * R + r])));
-        f.ll()[j * R + r] = f2(df_fma(fp(f.cpL()[j]), eL, fp(f.ll()[j * R + r])));
+        f.lr()[(j + 1) * RP + r] = f2(mfma<PAIR>(mld<PAIR>(&f.cpR()[j]), eR, mld<PAIR>(&f.lr()[(j + 1) * RP + r])));
+        f.ll()[j * RP + r] = f2(mfma<PAIR>(mld<PAIR>(&f.cpL()[j]), eL, mld<PAIR>(&f.ll()[j * RP + r])));
       }
     } else if (j0 < m) {   // one block per lane: the scan already holds the values
-      f.lr()[(j0 + 1) * R + r] = f2(accR);
-      f.ll()[j0 * R + r] = f2(accL);
+      f.lr()[(j0 + 1) * RP + r] = f2(accR);
+      f.ll()[j0 * RP + r] = f2(accL);
     }
     if (lane == 0) {
       f.lr()[r] = make_float2(0.f, 0.f);
-      f.ll()[m * R + r] = make_float2(0.f, 0.f);
+      f.ll()[m * RP + r] = make_float2(0.f, 0.f);
     }
     __syncwarp();
     if (lane == 0) {
-      f.xch()[(parity * 2 + 0) * R + r] = f.lr()[m * R + r];
+      f.xch()[(parity * 2 + 0) * R + r] = f.lr()[m * RP + r];
       f.xch()[(parity * 2 + 1) * R + r] = f.ll()[r];
     }
   }
@@ -257,7 +296,7 @@ __device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM>& f, int m, in
 // in_R, in_L of every column from the other CTAs' totals (after a cluster
 // barrier): one warp per column, lanes 0-15 for the CTAs to the left, 16-31
 // for those to the right.
-template <int R, int MM>
+template <int R, int MM, bool PAIR = true>
 __device__ __forceinline__ void iface_df_fold(const IfaceDF<R, MM>& f, int C, unsigned c, int parity) {
   const int lane = threadIdx.x & 31, cc = lane & 15;
   const bool left = lane < 16;
@@ -266,21 +305,22 @@ __device__ __forceinline__ void iface_df_fold(const IfaceDF<R, MM>& f, int C, un
     f2pair v{0.f, 0.f};
     if (valid) {
       const float2 x = ld_cluster_f32x2(f.xch() + (parity * 2 + (left ? 0 : 1)) * R + r, (unsigned)cc);
-      v = df_fma(fp(left ? f.wR()[cc] : f.wL()[cc]), fp(x), f2pair{0.f, 0.f});
+      v = mfma<PAIR>(mld<PAIR>(left ? &f.wR()[cc] : &f.wL()[cc]), fp(x), f2pair{0.f, 0.f});
     }
 #pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) v = df_add(v, shfl_xor_pair(v, o));
+    for (int o = 8; o >= 1; o >>= 1) v = madd<PAIR>(v, mshfl_xor<PAIR>(v, o));
     if (lane == 0) f.in()[r] = f2(v);
     if (lane == 16) f.in()[R + r] = f2(v);
   }
 }
 
 // x(p_j) for column r, rounded to binary32
-template <int R, int MM>
+template <int R, int MM, bool PAIR = true>
 __device__ __forceinline__ float iface_df_sep(const IfaceDF<R, MM>& f, int j, int r) {
-  f2pair x = df_add(fp(f.lr()[j * R + r]), fp(f.ll()[j * R + r]));
-  x = df_fma(fp(f.piR()[j]), fp(f.in()[r]), x);
-  x = df_fma(fp(f.piL()[j]), fp(f.in()[R + r]), x);
+  constexpr int RP = IfaceDF<R, MM>::kRP;
+  f2pair x = madd<PAIR>(mld<PAIR>(&f.lr()[j * RP + r]), mld<PAIR>(&f.ll()[j * RP + r]));
+  x = mfma<PAIR>(mld<PAIR>(&f.piR()[j]), mld<PAIR>(&f.in()[r]), x);
+  x = mfma<PAIR>(mld<PAIR>(&f.piL()[j]), mld<PAIR>(&f.in()[R + r]), x);
   return x.h + x.l;
 }
 

@@ -55,24 +55,64 @@ using namespace tdmk;
 constexpr float kRefineTol = 1e-12f;
 
 // max over columns of (max|d| / max|x|) over the whole cluster; every thread of
-// every CTA gets the same value (exact maxima read in the same order).
+// every CTA gets the same value (exact maxima, the same division).  slot holds
+// this CTA's per-column maxima [2][R]; one warp per column reads every CTA's
+// pair in one round (lanes 0-15: max|d|, lanes 16-31: max|x|).
 template <int R>
-__device__ __forceinline__ float cluster_ratio(const float* slot, int C, int tid, float* bcast) {
-  if (tid < 32) {
+__device__ __forceinline__ float cluster_ratio(const float* slot, int C, int tid, float* scratch, float* bcast) {
+  const int lane = tid & 31, nwarps = blockDim.x >> 5;
+  for (int col = tid >> 5; col < R; col += nwarps) {
+    const int cc = lane & 15;
+    float v = cc < C ? ld_cluster_f32(slot + (lane >> 4) * R + col, (unsigned)cc) : 0.f;
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const float mx = __shfl_sync(0xffffffffu, v, 16);
+    if (lane == 0) scratch[col] = mx > 0.f ? v / mx : 0.f;
+  }
+  __syncthreads();
+  if (tid == 0) {
     float q = 0.f;
-    if (tid < R) {
-      float md = 0.f, mx = 0.f;
-      for (int cc = 0; cc < C; cc++) {
-        md = fmaxf(md, ld_cluster_f32(slot + tid, (unsigned)cc));
-        mx = fmaxf(mx, ld_cluster_f32(slot + R + tid, (unsigned)cc));
-      }
-      q = mx > 0.f ? md / mx : 0.f;
-    }
-    for (int o = 16; o > 0; o >>= 1) q = fmaxf(q, __shfl_xor_sync(0xffffffffu, q, o));
-    if (tid == 0) *bcast = q;
+    for (int k = 0; k < R; k++) q = fmaxf(q, scratch[k]);
+    *bcast = q;
   }
   __syncthreads();
   return *bcast;
+}
+
+// per-CTA, per-column maxima of |d| and |x0| into slot [2][R]: shuffles over
+// the blocks a warp covers, then over the warps
+template <int R>
+__device__ __forceinline__ void cta_maxima(float md, float mx, float* red, float* slot, int tid) {
+  const int lane = tid & 31, nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int o = R; o < 32; o <<= 1) {
+    md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane < R) {
+    red[(tid >> 5) * R + lane] = md;
+    red[(nwarps + (tid >> 5)) * R + lane] = mx;
+  }
+  __syncthreads();
+  if (tid < R) {
+    float a = 0.f, b = 0.f;
+    for (int w = 0; w < nwarps; w++) {
+      a = fmaxf(a, red[w * R + tid]);
+      b = fmaxf(b, red[(nwarps + w) * R + tid]);
+    }
+    slot[tid] = a;
+    slot[R + tid] = b;
+  }
+}
+
+// The two halves of a cluster barrier, for work that overlaps its completion:
+// arrive after the writes the other CTAs will read (release), wait before
+// reading theirs (acquire).  Every thread of every CTA executes both.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // streaming loads/stores for the right-hand sides and the solution: they are
@@ -131,50 +171,118 @@ __device__ __forceinline__ void load_rhs(float (&g)[TT], const float* Fp, int64_
 
 // Residual r = F - A x of the iterate x = x0 + delta over one block, in
 // row-sum form: r_i = F_i - sigma_i x_i + E_{i-1} - E_i with the fluxes
-// E_i = a_i (x_{i+1} - x_i).  g holds F on entry and r on exit.  Ep is the
-// flux into the block's first row; xp is x at the row after the block.
-// FIRST: delta is still zero (first correction), so the differences of x are
-// single TwoSums and sigma x a pair-by-float product.  Rows past n carry zero
-// coefficients, F and x, so they add nothing.
+// E_i = a_i (x_{i+1} - x_i).  g holds F on entry and r on exit.  FIRST: delta
+// is still zero (first correction), so the differences of x are single
+// TwoSums and sigma x a pair-by-float product.  Rows past n carry zero
+// coefficients, F and x, so they add nothing.  The rows are done in two parts
+// so that the interior (rows 1 .. TT-2, this block's iterate only) can run
+// while the cluster barrier that publishes the neighbours' edge values
+// completes; rows 0 and TT-1 follow.
+
+// r_i from F_i, the fluxes on both sides of row i and sigma_i x_i (the large
+// fluxes cancel exactly in the first TwoSum)
+__device__ __forceinline__ float residual_row(float Fi, f2pair Ep, f2pair E, f2pair S) {
+  const f2pair w = two_sum_f(Ep.h, -E.h);
+  const f2pair u = two_sum_f(Fi, w.h);
+  const f2pair v = two_sum_f(u.h, -S.h);
+  const float small = ((Ep.l - E.l) - S.l) + (w.l + u.l + v.l);
+  return v.h + small;
+}
+template <bool FIRST>
+__device__ __forceinline__ f2pair x_diff(f2pair x1, f2pair x0) {
+  if constexpr (FIRST) return two_sum_f(x1.h, -x0.h);
+  else return df_diff(x1, x0);
+}
+template <bool FIRST>
+__device__ __forceinline__ f2pair sigma_x(float sh, float sl, f2pair x) {
+  if constexpr (FIRST) return df_mul_f(f2pair{sh, sl}, x.h);
+  else return df_mul(f2pair{sh, sl}, x);
+}
+template <int R, bool FIRST>
+__device__ __forceinline__ f2pair x_at(const float* x0, const float* delta, int i) {
+  return f2pair{x0[i], FIRST ? 0.f : delta[i * R]};
+}
+
+// rows 1 .. TT-2; returns E_0 and E_{TT-2} for the edge rows
 template <int R, int TT, bool FULL, bool FIRST, bool SM, int RS>
-__device__ __forceinline__ void residual_block(float (&g)[TT], const float (&x0)[TT], const float* delta,
-                                               const float* rsb, f2pair Ep, f2pair xp, int nrows) {
-  f2pair xi{x0[0], FIRST ? 0.f : delta[0]};
+__device__ __forceinline__ void residual_interior(float (&g)[TT], const float (&x0)[TT], const float* delta,
+                                                  const float* rsb, int nrows, f2pair& E0, f2pair& Elast) {
+  float sh, sl, ah = 0.f, al = 0.f;
+  if (FULL || 0 < nrows) cld4<SM>(rsb, sh, sl, ah, al);   // kS0, kS1, kA0, kA1 of row 0
+  f2pair xi = f2pair{x0[1], FIRST ? 0.f : delta[R]};
+  f2pair Ep = df_mul(f2pair{ah, al}, x_diff<FIRST>(xi, f2pair{x0[0], FIRST ? 0.f : delta[0]}));
+  E0 = Ep;
 #pragma unroll
-  for (int i = 0; i < TT; i++) {
-    float sh = 0.f, sl = 0.f, ah = 0.f, al = 0.f;
-    if (FULL || i < nrows) cld4<SM>(rsb + i * RS, sh, sl, ah, al);   // kS0, kS1, kA0, kA1
-    const f2pair xn = (i + 1 < TT) ? f2pair{x0[i + 1], FIRST ? 0.f : delta[(i + 1) * R]} : xp;
-    const f2pair E = df_mul(f2pair{ah, al}, FIRST ? two_sum_f(xn.h, -xi.h) : df_diff(xn, xi));
-    const f2pair S = FIRST ? df_mul_f(f2pair{sh, sl}, xi.h) : df_mul(f2pair{sh, sl}, xi);
-    const f2pair w = two_sum_f(Ep.h, -E.h);
-    const f2pair u = two_sum_f(g[i], w.h);
-    const f2pair v = two_sum_f(u.h, -S.h);
-    const float small = ((Ep.l - E.l) - S.l) + (w.l + u.l + v.l);
-    g[i] = v.h + small;
+  for (int i = 1; i < TT - 1; i++) {
+    sh = sl = ah = al = 0.f;
+    if (FULL || i < nrows) cld4<SM>(rsb + i * RS, sh, sl, ah, al);
+    const f2pair xn = f2pair{x0[i + 1], FIRST ? 0.f : delta[(i + 1) * R]};
+    const f2pair E = df_mul(f2pair{ah, al}, x_diff<FIRST>(xn, xi));
+    g[i] = residual_row(g[i], Ep, E, sigma_x<FIRST>(sh, sl, xi));
     Ep = E;
     xi = xn;
   }
+  Elast = Ep;
 }
 
-// A5 of a solve: back substitution and correction with the separator values.
-// The iterate is x = x0 + delta: x0 (registers) is the first solve's result,
-// delta (shared memory, stride R) accumulates the corrections.
+// rows 0 and TT-1, with x at the rows just outside the block (xm, xp) and
+// a_{row0-1} (aprev)
+template <int R, int TT, bool FULL, bool FIRST, bool SM, int RS>
+__device__ __forceinline__ void residual_edges(float (&g)[TT], const float (&x0)[TT], const float* delta,
+                                               const float* rsb, int nrows, f2pair aprev, f2pair xm, f2pair xp,
+                                               f2pair E0, f2pair Elast) {
+  float sh = 0.f, sl = 0.f, ah = 0.f, al = 0.f;
+  const f2pair x_first = f2pair{x0[0], FIRST ? 0.f : delta[0]};
+  if (FULL || 0 < nrows) cld4<SM>(rsb, sh, sl, ah, al);
+  const f2pair Em1 = df_mul(aprev, x_diff<FIRST>(x_first, xm));
+  g[0] = residual_row(g[0], Em1, E0, sigma_x<FIRST>(sh, sl, x_first));
+  sh = sl = ah = al = 0.f;
+  if (FULL || TT - 1 < nrows) cld4<SM>(rsb + (TT - 1) * RS, sh, sl, ah, al);
+  const f2pair x_last = f2pair{x0[TT - 1], FIRST ? 0.f : delta[(TT - 1) * R]};
+  const f2pair E = df_mul(f2pair{ah, al}, x_diff<FIRST>(xp, x_last));
+  g[TT - 1] = residual_row(g[TT - 1], Elast, E, sigma_x<FIRST>(sh, sl, x_last));
+}
+
+// A5 of a solve, in two parts.  The back substitution of the block's local
+// sweep does not depend on the separator values, so it runs while the cluster
+// barrier of A4 completes; y replaces g.
+template <bool SM>
+__device__ __forceinline__ void cld2(const float* p, float& x, float& y) {
+  float2 v;
+  if constexpr (SM) v = *reinterpret_cast<const float2*>(p);
+  else v = __ldg(reinterpret_cast<const float2*>(p));
+  x = v.x;
+  y = v.y;
+}
+template <int TT, bool FULL, bool SM>
+__device__ __forceinline__ void backward_y(float (&g)[TT], const float* cf, int nrows) {
+  float y = 0.f;
+#pragma unroll
+  for (int i = TT - 1; i >= 0; i--) {
+    if (FULL || i < nrows) {
+      float cc, invd;
+      cld2<SM>(cf + i * kNCOEF + kC, cc, invd);
+      y = fmaf(-cc, y, g[i]) * invd;
+      g[i] = y;
+    }
+  }
+}
+// Then the correction with the separator values, d = y + phiL xL + phiR xR,
+// and the update of the iterate x = x0 + delta: x0 (registers) is the first
+// solve's result, delta (shared memory, stride R) accumulates the corrections.
 //   FIRST (the first solve): x0 = d, g = 0.
 //   otherwise: d is added to delta with Knuth's TwoSum; its exact rounding
 //   error replaces g[i], so that the output can include the last one.
 // TRACK: maxd = max |d| over the block (for the convergence test).
 template <int R, int TT, bool FULL, bool SM, bool FIRST, bool TRACK>
-__device__ __forceinline__ void backward_update(float (&g)[TT], const float* cf, int nrows, float xL, float xR,
-                                                float (&x0)[TT], float* delta, float& maxd) {
-  float y = 0.f;
+__device__ __forceinline__ void backward_d(float (&g)[TT], const float* cf, int nrows, float xL, float xR,
+                                           float (&x0)[TT], float* delta, float& maxd) {
 #pragma unroll
-  for (int i = TT - 1; i >= 0; i--) {
+  for (int i = 0; i < TT; i++) {
     if (FULL || i < nrows) {
-      float cc, invd, phl, phr;
-      cld4<SM>(cf + i * kNCOEF + 4, cc, invd, phl, phr);
-      y = fmaf(-cc, y, g[i]) * invd;
-      const float d = fmaf(phr, xR, fmaf(phl, xL, y));
+      float phl, phr;
+      cld2<SM>(cf + i * kNCOEF + kPHIL, phl, phr);
+      const float d = fmaf(phr, xR, fmaf(phl, xL, g[i]));
       if (FIRST) {
         x0[i] = d;
         g[i] = 0.f;
@@ -189,11 +297,11 @@ __device__ __forceinline__ void backward_update(float (&g)[TT], const float* cf,
 }
 
 template <int R, int TT, bool FULL, bool SM>
-__device__ __forceinline__ void backward_any(bool first, bool track, float (&g)[TT], const float* cf, int nrows,
-                                             float xL, float xR, float (&x0)[TT], float* delta, float& maxd) {
-  if (first) backward_update<R, TT, FULL, SM, true, true>(g, cf, nrows, xL, xR, x0, delta, maxd);
-  else if (track) backward_update<R, TT, FULL, SM, false, true>(g, cf, nrows, xL, xR, x0, delta, maxd);
-  else backward_update<R, TT, FULL, SM, false, false>(g, cf, nrows, xL, xR, x0, delta, maxd);
+__device__ __forceinline__ void backward_d_any(bool first, bool track, float (&g)[TT], const float* cf, int nrows,
+                                               float xL, float xR, float (&x0)[TT], float* delta, float& maxd) {
+  if (first) backward_d<R, TT, FULL, SM, true, true>(g, cf, nrows, xL, xR, x0, delta, maxd);
+  else if (track) backward_d<R, TT, FULL, SM, false, true>(g, cf, nrows, xL, xR, x0, delta, maxd);
+  else backward_d<R, TT, FULL, SM, false, false>(g, cf, nrows, xL, xR, x0, delta, maxd);
 }
 
 // floats per block of the staged solve coefficients (16 bytes of padding)
@@ -212,7 +320,7 @@ __host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, b
   o.delta = p; p += round16(4 * MM * (TT + 1) * R);
   o.edge = p; p += round16(4 * 4 * MM * R);
   o.red = p; p += round16(4 * 2 * MM * R);
-  o.cvg = p; p += round16(4 * 4 * (size_t)R);
+  o.cvg = p; p += round16(4 * 5 * (size_t)R);
   o.coef = p; if (sm_coef) p += round16(4 * MM * (TT * kNCOEF + 4));
   o.res = p; if (sm_coef) p += round16(16 * MM * (TT + 1));
   o.pad = p; if (sm_coef) p += round16(4 * (size_t)(TT + 1) * R);   // delta words of threads past the blocks
@@ -237,9 +345,9 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   float* const eFl = eFh + MM * R;
   float* const eLh = eFl + MM * R;
   float* const eLl = eLh + MM * R;
-  float* const redD = reinterpret_cast<float*>(smem_raw + O.red);    // [2][MM][R] per-block maxima
-  float* const redX = redD + MM * R;
+  float* const redD = reinterpret_cast<float*>(smem_raw + O.red);    // [2][warps][R] per-warp maxima
   float* const cvg = reinterpret_cast<float*>(smem_raw + O.cvg);     // [2][2][R] per-CTA maxima, read remotely
+  float* const cvg_scratch = cvg + 4 * R;                            // [R]
   // SM: the CTA's coefficient rows, reloaded when the series changes
   float* const scf = reinterpret_cast<float*>(smem_raw + O.coef);    // [MM][TT*8+4]
   float* const sres = reinterpret_cast<float*>(smem_raw + O.res);    // [MM][TT+1][4]
@@ -330,18 +438,37 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
           eFh[bl * R + r] = xh[0]; eFl[bl * R + r] = xlt[0];
           eLh[bl * R + r] = xh[TT - 1]; eLl[bl * R + r] = xlt[(TT - 1) * R];
         }
-        cluster_barrier();
-        if (adaptive && step >= 2) {   // converged after the previous correction?
-          // after the first correction there is no contraction estimate yet: stop only if
-          // the correction itself is below the tolerance
-          const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, L.C, tid, &ratio_s);
-          const bool stop = (step == 2) ? (ratio <= kRefineTol) : (ratio * ratio <= kRefineTol * ratio_prev);
+        // Adaptive refinement makes at least two corrections; from the third
+        // step on it first tests the last one (estimated error
+        // ratio_k^2 / ratio_{k-1}), which needs every CTA's maxima.  Otherwise
+        // the interior of the residual overlaps the edge-value barrier.
+        const bool test = adaptive && step >= 3;
+        if (test) {
+          cluster_barrier();
+          if (step == 3) ratio_prev = cluster_ratio<R>(cvg + cpar * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
+          const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
+          const bool stop = ratio * ratio <= kRefineTol * ratio_prev;
           ratio_prev = ratio;
           if (stop) break;
+        } else {
+          cluster_arrive();
         }
+        f2pair E0{0.f, 0.f}, Elast{0.f, 0.f};
         if (bl < m) {
           if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
           else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
+          if (nrows > 0) {
+            if (step == 1) {   // delta is still zero
+              if (SM || full) residual_interior<R, TT, true, true, SM, RS>(g, xh, xlt, rsb, nrows, E0, Elast);
+              else residual_interior<R, TT, SM, true, SM, RS>(g, xh, xlt, rsb, nrows, E0, Elast);
+            } else {
+              if (SM || full) residual_interior<R, TT, true, false, SM, RS>(g, xh, xlt, rsb, nrows, E0, Elast);
+              else residual_interior<R, TT, SM, false, SM, RS>(g, xh, xlt, rsb, nrows, E0, Elast);
+            }
+          }
+        }
+        if (!test) cluster_wait();
+        if (bl < m) {
           f2pair xm{0.f, 0.f}, xp{0.f, 0.f};   // x at rows row0-1 and row0+TT
           if (bl > 0) {
             xm = f2pair{eLh[(bl - 1) * R + r], eLl[(bl - 1) * R + r]};
@@ -354,18 +481,15 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
             xp = f2pair{ld_cluster_f32(eFh + r, c + 1), ld_cluster_f32(eFl + r, c + 1)};
           }
           if (nrows > 0) {
-            // flux into the first row: E_{row0-1} = a_{row0-1} (x_row0 - x_{row0-1})
-            float a_h = 0.f, a_l = 0.f;
-            if (row0 > 0) { a_h = rsb[-RS + kA0]; a_l = rsb[-RS + kA1]; }
-            const f2pair xi{xh[0], xlt[0]};
-            if (step == 1) {   // delta is still zero
-              const f2pair Ep = df_mul(f2pair{a_h, a_l}, two_sum_f(xi.h, -xm.h));
-              if (SM || full) residual_block<R, TT, true, true, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
-              else residual_block<R, TT, SM, true, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
+            // a_{row0-1}, for the flux into the first row
+            f2pair aprev{0.f, 0.f};
+            if (row0 > 0) aprev = f2pair{rsb[-RS + kA0], rsb[-RS + kA1]};
+            if (step == 1) {
+              if (SM || full) residual_edges<R, TT, true, true, SM, RS>(g, xh, xlt, rsb, nrows, aprev, xm, xp, E0, Elast);
+              else residual_edges<R, TT, SM, true, SM, RS>(g, xh, xlt, rsb, nrows, aprev, xm, xp, E0, Elast);
             } else {
-              const f2pair Ep = df_mul(f2pair{a_h, a_l}, df_diff(xi, xm));
-              if (SM || full) residual_block<R, TT, true, false, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
-              else residual_block<R, TT, SM, false, SM, RS>(g, xh, xlt, rsb, Ep, xp, nrows);
+              if (SM || full) residual_edges<R, TT, true, false, SM, RS>(g, xh, xlt, rsb, nrows, aprev, xm, xp, E0, Elast);
+              else residual_edges<R, TT, SM, false, SM, RS>(g, xh, xlt, rsb, nrows, aprev, xm, xp, E0, Elast);
             }
           }
         }
@@ -375,12 +499,15 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       if (SM || full) forward_pass_g<TT, true, SM>(g, cfb, nrows, bR, bL);
       else forward_pass_g<TT, SM, SM>(g, cfb, nrows, bR, bL);
       if (bl < m) {
-        f.beR()[bl * R + r] = bR;
-        f.beL()[bl * R + r] = bL;
+        f.beR()[bl * f.kRP + r] = bR;
+        f.beL()[bl * f.kRP + r] = bL;
       }
       __syncthreads();
       iface_df_scan<R>(f, m, parity);
-      cluster_barrier();
+      cluster_arrive();   // the back substitution overlaps the exchange of the CTA totals
+      if (SM || full) backward_y<TT, true, SM>(g, cfb, nrows);
+      else backward_y<TT, SM, SM>(g, cfb, nrows);
+      cluster_wait();
       iface_df_fold<R>(f, L.C, c, parity);
       __syncthreads();
       parity ^= 1;
@@ -391,26 +518,21 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       }
       float maxd = 0.f;
       const bool first = step == 0;
-      if (SM || full) backward_any<R, TT, true, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
-      else backward_any<R, TT, SM, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
+      if (SM || full) backward_d_any<R, TT, true, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
+      else backward_d_any<R, TT, SM, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
       if (!col_ok) maxd = 0.f;   // padding columns of a ragged tile do not vote
       if (first) {
         maxx = maxd;
       } else if (adaptive) {   // per-CTA, per-column maxima of |d| and |x0| for the test
-        if (bl < m) { redD[bl * R + r] = maxd; redX[bl * R + r] = maxx; }
-        __syncthreads();
-        if (tid < R) {
-          float md = 0.f, mx = 0.f;
-          for (int j = 0; j < m; j++) { md = fmaxf(md, redD[j * R + tid]); mx = fmaxf(mx, redX[j * R + tid]); }
-          cvg[cpar * 2 * R + tid] = md;
-          cvg[cpar * 2 * R + R + tid] = mx;
-        }
+        cta_maxima<R>(maxd, maxx, redD, cvg + cpar * 2 * R, tid);
         cpar ^= 1;
       }
       if (step == cap) {
         if (adaptive) {   // cap reached: record whether the last correction met the test
           cluster_barrier();
-          const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, L.C, tid, &ratio_s);
+          if (step < 3) ratio_prev = step == 2 ? cluster_ratio<R>(cvg + cpar * 2 * R, L.C, tid, cvg_scratch, &ratio_s)
+                                               : 1.f;
+          const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
           if (tid == 0 && !(ratio * ratio <= kRefineTol * ratio_prev)) atomicExch(L.err, kDevErrNotConverged);
         }
         break;

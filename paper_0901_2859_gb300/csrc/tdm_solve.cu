@@ -73,6 +73,7 @@ bool tdm_encode_tma_2d(CUtensorMap* out, const void* base, bool fp64, uint64_t c
 }
 
 #include "tdm_kernel_common.cuh"
+#include "tdm_iface_df.cuh"
 
 namespace {
 using namespace tdmk;
@@ -85,8 +86,13 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
   unsigned char* base = smem_raw + smem_align_pad(smem_raw);
   T* fbuf = reinterpret_cast<T*>(base);
   T* scf = reinterpret_cast<T*>(base + fbuf_bytes(a.m, TT, R, (int)sizeof(T), TMA));   // [m*t][8]
-  const Smem s = carve(reinterpret_cast<unsigned char*>(scf) + coef_bytes(a.m, TT, (int)sizeof(T)), a.m, R,
-                       (int)sizeof(T));
+  // A4 state: binary64 recurrences for the binary64 solve; for the binary32
+  // solve, binary32 scans over the same precomputed products as the refined
+  // kernel (its separator values only need binary32 accuracy)
+  unsigned char* const a4 = reinterpret_cast<unsigned char*>(scf) + coef_bytes(a.m, TT, (int)sizeof(T));
+  const Smem s = carve(a4, a.m, R, (int)sizeof(T));
+  constexpr int MM = MAXT / R;
+  const IfaceDF<R, MM> f{a4};
   const unsigned c = cluster_rank();
   const int tid = threadIdx.x;
   const int r = tid % R;
@@ -103,7 +109,8 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
   const T* __restrict__ coef = static_cast<const T*>(a.coef);
   const int n = a.n;
 
-  setup_ratios(a, s, c);
+  if constexpr (sizeof(T) == 8) setup_ratios(a, s, c);
+  else iface_df_setup(f, a.rR, a.rL, a.M, a.m, a.C, c);
   {   // this CTA's coefficient rows stay in shared memory for every tile
     const int nvec = rows_cta * kNCOEF / 4;
     for (int k = tid; k < nvec; k += blockDim.x) {
@@ -157,18 +164,34 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
     T bR = T(0), bL = T(0);
     if (nrows == TT) forward_pass<T, TT, true>(v, cfb, nrows, bR, bL);
     else forward_pass<T, TT, false>(v, cfb, nrows, bR, bL);
-    if (bl < a.m) {
-      s.betaR[bl * R + r] = tdm_to_f64<T>(bR);
-      s.betaL[bl * R + r] = tdm_to_f64<T>(bL);
-    }
-    __syncthreads();
-    separator_partials<T, R>(a, s, c, parity);
-    // A5: back substitution + correction + store
     T xL = T(0), xR = T(0);
-    if (blk_ok) {
-      if (b >= 1) xL = separator_value<T, R>(s, bl, r);
-      if (b + 1 <= a.M - 1) xR = separator_value<T, R>(s, bl + 1, r);
+    if constexpr (sizeof(T) == 8) {
+      if (bl < a.m) {
+        s.betaR[bl * R + r] = bR;
+        s.betaL[bl * R + r] = bL;
+      }
+      __syncthreads();
+      separator_partials<T, R>(a, s, c, parity);
+      if (blk_ok) {
+        if (b >= 1) xL = separator_value<T, R>(s, bl, r);
+        if (b + 1 <= a.M - 1) xR = separator_value<T, R>(s, bl + 1, r);
+      }
+    } else {
+      if (bl < a.m) {
+        f.beR()[bl * f.kRP + r] = bR;
+        f.beL()[bl * f.kRP + r] = bL;
+      }
+      __syncthreads();
+      iface_df_scan<R, MM, false>(f, a.m, parity);
+      cluster_barrier();
+      iface_df_fold<R, MM, false>(f, a.C, c, parity);
+      __syncthreads();
+      if (blk_ok) {
+        if (b >= 1) xL = iface_df_sep<R, MM, false>(f, bl, r);
+        if (b + 1 <= a.M - 1) xR = iface_df_sep<R, MM, false>(f, bl + 1, r);
+      }
     }
+    // A5: back substitution + correction + store
     T* Xp = X + row0 * a.ldX + col;
     if (nrows == TT) backward_store<T, TT, true>(v, cfb, nrows, xL, xR, Xp, a.ldX, col_ok);
     else backward_store<T, TT, false>(v, cfb, nrows, xL, xR, Xp, a.ldX, col_ok);
@@ -288,10 +311,16 @@ tdm_status tdm_launch_plain(tdm_plan_s* p, const void* F, int64_t ldF, void* X, 
   cfg.tma = env_int("TDM_NO_TMA", 0) == 0 &&
             tdm_encode_tma_2d(&map, F, fp64, (uint64_t)N, (uint64_t)p->n, (uint64_t)ldF * tsize,
                               (uint32_t)cfg.R, (uint32_t)cfg.box_rows);
-  cfg.smem = smem_bytes(cfg.m, p->t, cfg.R, tsize, cfg.tma);
+  // the binary32 solve keeps its A4 arrays in the pair layout, sized for 512 / R blocks
+  auto bytes = [&](bool tma) {
+    return fp64 ? smem_bytes(cfg.m, p->t, cfg.R, tsize, tma)
+                : 128 + fbuf_bytes(cfg.m, p->t, cfg.R, tsize, tma) + coef_bytes(cfg.m, p->t, tsize) +
+                      iface_offsets(cfg.R, 512 / cfg.R).bytes;
+  };
+  cfg.smem = bytes(cfg.tma);
   if (cfg.smem > 227 * 1024) {   // fall back to direct loads when the staging buffer does not fit
     cfg.tma = false;
-    cfg.smem = smem_bytes(cfg.m, p->t, cfg.R, tsize, false);
+    cfg.smem = bytes(false);
   }
   SolveArgs args;
   args.F = F; args.X = X; args.ldF = ldF; args.ldX = ldX; args.N = N;
