@@ -369,6 +369,7 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   int cur_series = -1;
   int parity = 0;
 
+  bool preloaded = false;   // g already holds this item's F (loaded during the previous output)
   for (int it = cluster_id; it < L.nitems; it += nclusters) {
     // fields of the current item, read where they are used (kernel parameter
     // or work list; no address of the parameter is taken)
@@ -425,8 +426,11 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       xh[i] = 0.f;
       if (SM || bl < m) xlt[i * R] = 0.f;
     }
-    if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
-    else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
+    if (!preloaded) {
+      if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
+      else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
+    }
+    bool have_f = false;   // g holds F for the next residual (loaded right after the last solve)
 
     float ratio_prev = 1.f;
     float maxx = 0.f;   // max |x0| of this thread's rows (the first solve)
@@ -455,8 +459,11 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
         }
         f2pair E0{0.f, 0.f}, Elast{0.f, 0.f};
         if (bl < m) {
-          if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
-          else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
+          if (!have_f) {
+            if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
+            else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
+          }
+          have_f = false;
           if (nrows > 0) {
             if (step == 1) {   // delta is still zero
               if (SM || full) residual_interior<R, TT, true, true, SM, RS>(g, xh, xlt, rsb, nrows, E0, Elast);
@@ -527,6 +534,14 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
         cta_maxima<R>(maxd, maxx, redD, cvg + cpar * 2 * R, tid);
         cpar ^= 1;
       }
+      // when another correction is certain, the last rounding errors in g are
+      // not needed: reload F now, so that the loads overlap the bookkeeping
+      // and the edge-value exchange
+      if (step < cap && (!adaptive || step < 2) && bl < m) {
+        if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
+        else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
+        have_f = true;
+      }
       if (step == cap) {
         if (adaptive) {   // cap reached: record whether the last correction met the test
           cluster_barrier();
@@ -539,16 +554,36 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       }
     }
     // ---- X = x0 + delta + (last rounding error, in g), rounded once to binary64 ----
-    if (active) {
+    // Each row's g is free once the row is stored: the next item's F row is
+    // loaded into it there, so that its latency overlaps the rest of the output.
+    {
+      const int it2 = it + nclusters;
+      preloaded = it2 < L.nitems;
+      const float* Fn = nullptr;
+      int64_t ldn = 0;
+      int nrows_n = 0;
+      if (preloaded) {
+#define ITEM2(f) (L.single ? L.one.f : L.items[it2].f)
+        const int tile_n = L.single ? it2 : L.items[it2].tile;
+        const int64_t col_n = (int64_t)tile_n * R + r;
+        const int n_n = ITEM2(n);
+        if ((bl < m) && (b < ITEM2(M)) && col_n < ITEM2(N)) {
+          nrows_n = (int)((n_n - row0) < TT ? (n_n - row0) : TT);
+          ldn = ITEM2(ldF);
+          Fn = ITEM2(F) + row0 * ldn + col_n;
+        }
+#undef ITEM2
+      }
       const int64_t ldX = ITEM(ldX);
       double* Xp = ITEM(X) + row0 * ldX + col;
 #pragma unroll
       for (int i = 0; i < TT; i++) {
-        if (full_rows || i < nrows) {
+        if (active && (full_rows || i < nrows)) {
           const f2pair sx = two_sum_f(xh[i], xlt[i * R]);
           st_stream(Xp, tdm_f2d(sx.h) + tdm_f2d(sx.l + g[i]));
         }
         Xp += ldX;
+        g[i] = i < nrows_n ? ld_stream(Fn + (int64_t)i * ldn) : 0.f;
       }
     }
   }
