@@ -75,10 +75,17 @@ typedef enum { TDM_FP64 = 0, TDM_FP32 = 1, TDM_FP32_REFINED = 2 } tdm_precision;
 typedef struct {
   int block_rows;    /* rows per block (the paper's subvector size); 0 = automatic (32).
                         Allowed: 16 or 32. */
-  int refine_steps;  /* TDM_FP32_REFINED corrections: k in 1..4 runs exactly k; 0 (automatic)
-                        makes at least two, then stops once the estimated relative error
-                        max|d_k|^2 / (max|x| max|d_{k-1}|) of the last correction is below
-                        1e-12; at most 4 corrections (device_error 2 otherwise) */
+  int refine_steps;  /* TDM_FP32_REFINED corrections:
+                          k in 1..4: exactly k;
+                          -1: every tile of right-hand sides tests its own: at least two, then
+                              stop once the estimated relative error
+                              max|d_k|^2 / (max|x| max|d_{k-1}|) of the last correction is
+                              below 1e-12; at most 4 (device_error 2 otherwise);
+                          0 (automatic): tdm_prepare solves 64 seeded right-hand sides with the
+                              per-tile test and fixes the plan's count to the most corrections
+                              any tile needed; -1 if that reached the cap or the plan is too
+                              large to calibrate cheaply (n > ~350000 uses fewer columns,
+                              n > ~2.8e6 none).  tdm_info reports the result. */
   int flags;         /* reserved, must be 0 */
   int reserved;
 } tdm_options;
@@ -89,7 +96,7 @@ typedef struct {
   int32_t num_blocks;      /* M = ceil(n / block_rows); separators = M - 1 */
   int32_t dominant;        /* 1 if |b_i| >= |a_{i-1}| + |a_i| for all i with one strict
                               inequality (Theorem 4: the method is then stable) */
-  int32_t refine_steps;    /* corrections of a TDM_FP32_REFINED solve; 0 = adaptive (at most 4) */
+  int32_t refine_steps;    /* corrections of a TDM_FP32_REFINED solve: 1..4, or -1 (tested per tile) */
   double max_abs_z;        /* max |Z^R|, |Z^L| ratio between neighbouring separators */
   double min_abs_pivot;    /* smallest |pivot| met in prepare, relative to ||A||_inf */
   int32_t device_error;    /* device-side error code of the last solves (0 = none,
@@ -108,7 +115,8 @@ typedef struct {
  *          tdm_destroy.  a and b may be freed after the call returns.
  * Errors: TDM_ERR_INVALID_ARG (n out of range, null pointers, 8-byte
  * misalignment), TDM_ERR_SINGULAR (nondegeneracy violated, Section 2),
- * TDM_ERR_NO_MEMORY, TDM_ERR_CUDA.  On error *out is set to NULL. */
+ * TDM_ERR_NO_MEMORY, TDM_ERR_CUDA.  On error *out is set to NULL.
+ * With refine_steps = 0 the call also runs one calibration solve (see tdm_options). */
 tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
                        const tdm_options* opt, void* stream, tdm_handle* out);
 

@@ -36,6 +36,7 @@
 
 #include "tdm_dd.cuh"
 #include "tdm_internal.cuh"
+#include "tdm_refine.cuh"
 
 namespace {
 
@@ -272,6 +273,64 @@ extern "C" tdm_status tdm_destroy(tdm_handle h) {
   return TDM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Automatic refinement (refine_steps = 0): one solve of seeded right-hand sides
+// with the per-tile test fixes the number of corrections of the plan to the
+// most that any tile needed.  The contraction of a correction is a property
+// of the matrix and of the binary32 solve, so later solves can skip the
+// cluster-wide test.  Plans too large for a cheap calibration, and matrices
+// whose calibration does not converge within the cap, keep the per-tile test.
+// ---------------------------------------------------------------------------
+namespace {
+
+// uniform pseudo-random values in [-1, 1) from an integer hash of the index
+__global__ void k_calib_rhs(float* F, int64_t count, uint32_t seed) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)k * 2654435761u ^ seed;
+    h ^= h >> 16; h *= 0x7feb352du; h ^= h >> 15; h *= 0x846ca68bu; h ^= h >> 16;
+    F[k] = (float)(int32_t)h * 4.656612873077393e-10f;
+  }
+}
+
+constexpr int kRefineAdaptive = -1;   // per-tile test
+constexpr size_t kCalibBytes = 256u << 20;
+
+tdm_status calibrate_refinement(tdm_plan_s* p, cudaStream_t s) {
+  p->refine_steps = kRefineAdaptive;
+  int N = 64;
+  while (N > 8 && (size_t)p->n * N * 12 > kCalibBytes) N /= 2;
+  if ((size_t)p->n * N * 12 > kCalibBytes) return TDM_OK;
+  RefShape sh;
+  if (!tdm_refined_shape(p->M, p->t, sh)) return TDM_OK;
+  float* F = nullptr;
+  double* X = nullptr;
+  tdm_status st = TDM_OK;
+  int h_used = 0, h_err = 0;
+  if (cudaMalloc(&F, sizeof(float) * p->n * N) != cudaSuccess || cudaMalloc(&X, sizeof(double) * p->n * N) != cudaSuccess) {
+    st = TDM_ERR_NO_MEMORY;
+  } else {
+    st = tdm_corrections_counter(true, nullptr, s);
+    cudaError_t e = cudaSuccess;
+    if (st == TDM_OK) {
+      k_calib_rhs<<<128, 256, 0, s>>>(F, p->n * N, 0x9e3779b9u);
+      const RefItem one = tdm_refined_item(p, F, N, X, N, N, 0);
+      st = tdm_refined_launch(sh, p->t, nullptr, &one, (N + sh.R - 1) / sh.R, p->dev_err, s);
+    }
+    if (st == TDM_OK) st = tdm_corrections_counter(false, &h_used, s);
+    if (st == TDM_OK) e = cudaMemcpyAsync(&h_err, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (st == TDM_OK && e == cudaSuccess) e = cudaMemsetAsync(p->dev_err, 0, sizeof(int), s);
+    if (st == TDM_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (st == TDM_OK && e != cudaSuccess) st = TDM_ERR_CUDA;
+  }
+  if (F) cudaFree(F);
+  if (X) cudaFree(X);
+  (void)cudaGetLastError();
+  if (st == TDM_OK && h_err == 0 && h_used >= 1 && h_used < 4) p->refine_steps = h_used;
+  return st;
+}
+
+}  // namespace
+
 extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
                                   const tdm_options* opt, void* stream, tdm_handle* out) {
   if (!out) return TDM_ERR_INVALID_ARG;
@@ -285,7 +344,7 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
     if (opt->refine_steps != 0) steps = opt->refine_steps;
   }
   if (t != 16 && t != 32) return TDM_ERR_INVALID_ARG;
-  if (steps < 0 || steps > 4) return TDM_ERR_INVALID_ARG;
+  if (steps < -1 || steps > 4) return TDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   (void)cudaGetLastError();   // report only errors of this call
 
@@ -351,6 +410,13 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
   if (flags & (kStatSingular | kStatNonFinite)) {
     tdm_free_plan(p);
     return TDM_ERR_SINGULAR;
+  }
+  if (steps == 0) {
+    const tdm_status st = calibrate_refinement(p, s);
+    if (st != TDM_OK) {
+      tdm_free_plan(p);
+      return st;
+    }
   }
   *out = p;
   return TDM_OK;

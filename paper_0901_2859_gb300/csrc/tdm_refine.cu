@@ -46,6 +46,11 @@
 #include "tdm_refine.cuh"
 #include "tdm_tma.cuh"
 
+// Most corrections any tile of a per-tile-tested launch has made on this
+// device since the counter was last cleared (read by the prepare-time
+// calibration; concurrent launches can only raise it).
+__device__ int g_tdm_corrections_max;
+
 namespace {
 using namespace tdmk;
 
@@ -453,7 +458,10 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
           const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
           const bool stop = ratio * ratio <= kRefineTol * ratio_prev;
           ratio_prev = ratio;
-          if (stop) break;
+          if (stop) {
+            if (tid == 0 && c == 0) atomicMax(&g_tdm_corrections_max, step - 1);
+            break;
+          }
         } else {
           cluster_arrive();
         }
@@ -549,6 +557,7 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
                                                : 1.f;
           const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
           if (tid == 0 && !(ratio * ratio <= kRefineTol * ratio_prev)) atomicExch(L.err, kDevErrNotConverged);
+          if (tid == 0 && c == 0) atomicMax(&g_tdm_corrections_max, cap);
         }
         break;
       }
@@ -711,4 +720,17 @@ tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double
   const RefItem one = tdm_refined_item(p, F, ldF, X, ldX, N, 0);
   const int ntiles = (int)((N + sh.R - 1) / sh.R);
   return tdm_refined_launch(sh, p->t, nullptr, &one, ntiles, p->dev_err, s);
+}
+
+// Clears / reads the corrections counter of the current device (calibration).
+tdm_status tdm_corrections_counter(bool clear, int* value, cudaStream_t s) {
+  if (clear) {
+    const int zero = 0;
+    TDM_CUDA_TRY(cudaMemcpyToSymbolAsync(g_tdm_corrections_max, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    TDM_CUDA_TRY(cudaStreamSynchronize(s));
+  } else {
+    TDM_CUDA_TRY(cudaMemcpyFromSymbolAsync(value, g_tdm_corrections_max, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    TDM_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return TDM_OK;
 }

@@ -41,5 +41,7 @@ bool tdm_refined_shape(int M, int t, RefShape& sh);
 // enqueue one launch over `nitems` items (items == nullptr: single series `one`)
 tdm_status tdm_refined_launch(const RefShape& sh, int t, const RefItem* items, const RefItem* one,
                               int nitems, int* err, cudaStream_t s);
+// the prepare-time calibration's view of the corrections per-tile-tested tiles made
+tdm_status tdm_corrections_counter(bool clear, int* value, cudaStream_t s);
 RefItem tdm_refined_item(const tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX,
                          int64_t N, int series);

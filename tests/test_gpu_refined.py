@@ -121,7 +121,7 @@ def test_refined_beats_plain_binary64_accuracy_when_ill_conditioned(tdm, dev, or
     assert e_ref <= TOL and e_ref < e_sweep
 
 
-@pytest.mark.parametrize("steps", [1, 3, 4])
+@pytest.mark.parametrize("steps", [-1, 1, 2, 3, 4])
 def test_refinement_step_counts(tdm, dev, oracle, steps):
     """A well-conditioned matrix reaches the gate with any step count >= 1."""
     from paper_0901_2859_gb300 import workloads
@@ -129,3 +129,29 @@ def test_refinement_step_counts(tdm, dev, oracle, steps):
     F32 = s.F.astype(np.float32)
     ref = oracle.solve_hi(s.a, s.b, F32.astype(np.float64))
     assert relerr(_refined(tdm, dev, s.a, s.b, F32, steps=steps), ref) <= TOL
+
+
+def test_automatic_refinement_is_calibrated_per_plan(tdm, dev, oracle):
+    """refine_steps = 0: prepare fixes the plan's correction count from a
+    calibration solve; the precision workload's worst case (s = 1e-6, kappa ~
+    3.9e6) needs two corrections and then meets the gate without a per-tile
+    test, exactly as the per-tile test (-1) does."""
+    from paper_0901_2859_gb300 import workloads
+    s = workloads.precision(seed=0, n=16384, N=64, s=1e-6)
+    auto = tdm.prepare(s.a, s.b, device=dev)
+    tested = tdm.prepare(s.a, s.b, refine_steps=-1, device=dev)
+    assert auto.info()["refine_steps"] == 2
+    assert tested.info()["refine_steps"] == -1
+    F = torch.from_numpy(s.F).to(dev)
+    Xa = auto.solve(F, "fp32_refined")
+    Xt = tested.solve(F, "fp32_refined")
+    torch.cuda.synchronize()
+    assert torch.equal(Xa, Xt)   # the per-tile test stops after the same two corrections
+    ref = oracle.solve_hi(s.a, s.b, s.F.astype(np.float64))
+    assert relerr(Xa.cpu().numpy(), ref) <= TOL
+    assert auto.info()["device_error"] == 0 and tested.info()["device_error"] == 0
+    well = workloads.plain_fp64(seed=4, n=1000, N=8)
+    p = tdm.prepare(well.a, well.b, device=dev)
+    assert 1 <= p.info()["refine_steps"] <= 3
+    for q in (auto, tested, p):
+        q.close()
