@@ -166,15 +166,17 @@ def _cpu_baseline(series, cols_target: int, X_gpu_cols=None):
            "sample": f"oracle binary64 sweep (thomas_f64) on the first {k} of {series.N} right-hand sides, "
                      f"n={series.n}, {dt:.2f} s"}
     if X_gpu_cols is not None:
-        idx, Xg = X_gpu_cols
+        idx, cols = X_gpu_cols
         ref = oracle.solve_hi(series.a, series.b, np.ascontiguousarray(series.F[:, idx], dtype=np.float64))
         den = np.maximum(np.abs(ref).max(axis=0), 1e-300)
-        out["refined_rel_err_vs_oracle"] = float(np.max(np.abs(Xg - ref).max(axis=0) / den))
+        for name, Xg in cols.items():   # relative max-norm error per column, max over the columns
+            out[f"{name}_rel_err_vs_oracle"] = float(np.max(np.abs(Xg - ref).max(axis=0) / den))
         out["error_columns"] = len(idx)
     return out
 
 
 def run_gpu(args):
+    N_RHS = args.rhs
     import numpy as np
     import torch
     import paper_0901_2859_gb300 as tdm
@@ -205,7 +207,7 @@ def run_gpu(args):
     hbm, peak_kind = _peaks()
     bytes_refined = unknowns * (4 + 8)
     achieved = bytes_refined / (ms * 1e-3) / 1e9
-    traffic = _traffic("k_solve_refined")
+    traffic = _traffic("k_refined")
 
     # ---- comparison paths: plain binary64 and plain binary32 dichotomy ------------------------
     F64 = F.double()
@@ -230,20 +232,23 @@ def run_gpu(args):
     # the refined solution of a few columns, for the accuracy check of the baseline leg
     plan.solve(F, "fp32_refined", out=X)
     idx = np.array([0, 1, 2, 3, N_RHS // 2, N_RHS - 1])
-    Xcols = X[:, idx].cpu().numpy()
+    Xcols = {"refined": X[:, idx].cpu().numpy()}
+    plan.solve(F.double(), "fp64", out=X)   # the plain binary64 path on the same columns
+    Xcols["fp64"] = X[:, idx].cpu().numpy()
     dev_err = plan.info()["device_error"]
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": DIST["world"], "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_ROWS, "N": N_RHS, "s": SHIFT, "precision": "fp32_refined",
+        "config": {"workload": WORKLOAD if N_RHS == 8192 else WORKLOAD.replace("N=8192", f"N={N_RHS}"),
+                   "n": N_ROWS, "N": N_RHS, "s": SHIFT, "precision": "fp32_refined",
                    "output": "f64", "refine_steps": info["refine_steps"], "block_rows": info["block_rows"],
                    "parallelism": f"rhs-sharded x{DIST['world']}" if DIST["world"] > 1 else "single GPU",
                    "l2": "no flush: F (512 MiB) and X (1 GiB) exceed L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": "k_solve_refined", "algorithmic_bytes_per_launch": bytes_refined},
+                     "kernel": "k_refined", "algorithmic_bytes_per_launch": bytes_refined},
         "e2e": {"value": DIST["world"] * unknowns / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": unknowns * 4, "d2h_bytes_per_step": unknowns * 8},
         "gpu_launches": args.steps,
@@ -270,6 +275,7 @@ def run_gpu(args):
 
 def run_reference(args):
     """The oracle (the plain CPU implementation), timed on the host cores on a bounded sample."""
+    N_RHS = args.rhs
     if DIST["rank"] != 0:
         return
     import numpy as np
@@ -310,6 +316,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-cols", type=int, default=2048, help="columns of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rhs", type=int, default=N_RHS,
+                    help="right-hand sides of the series (the benchmark is 8192; smaller values are for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
