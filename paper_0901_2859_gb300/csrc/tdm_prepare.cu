@@ -67,37 +67,102 @@ __global__ void k_norm_and_dominance(const double* __restrict__ a, const double*
   atomic_max_pos(&stat[1], rmax);
 }
 
-// Thread 0 sweeps from the top (dF), thread 1 from the bottom (dB), in double-double.
-__global__ void k_pivots(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
-                         dd* __restrict__ dF, dd* __restrict__ dB, unsigned long long* stat) {
+// Pivots of the sweep of A from the top (block 0: dF_i = b_i - a_{i-1}^2 / dF_{i-1})
+// and from the bottom (block 1: dB_i = b_i - a_i^2 / dB_{i+1}), in double-double.
+// A step d -> b - a^2 / d is linear fractional: with d = p / q it is
+// (p, q) -> (b p - a^2 q, p), a 2x2 matrix.  The rows are cut into one chunk per
+// thread; each thread multiplies its chunk's matrices (no division; rescaled
+// by powers of two, which leaves p / q unchanged), one thread carries the
+// state through the chunk products to find every chunk's incoming pivot, and
+// every thread then runs the recurrence itself over its chunk.
+struct dd2x2 {
+  dd m00, m01, m10, m11;
+};
+__device__ __forceinline__ void mob_step(dd2x2& C, double bi, dd a2) {   // C <- [[b, -a^2], [1, 0]] C
+  const dd n00 = dd_sub(dd_mul_d(C.m00, bi), dd_mul(a2, C.m10));
+  const dd n01 = dd_sub(dd_mul_d(C.m01, bi), dd_mul(a2, C.m11));
+  C.m10 = C.m00;
+  C.m11 = C.m01;
+  C.m00 = n00;
+  C.m01 = n01;
+}
+__device__ __forceinline__ dd dd_scale(dd x, double s) { return dd{x.hi * s, x.lo * s}; }   // s a power of two
+__device__ __forceinline__ double pow2_near_inverse(double mx) {
+  int e;
+  frexp(mx, &e);
+  return ldexp(1.0, -e);
+}
+__device__ __forceinline__ void mob_rescale(dd2x2& C) {
+  const double mx = fmax(fmax(fabs(C.m00.hi), fabs(C.m01.hi)), fmax(fabs(C.m10.hi), fabs(C.m11.hi)));
+  if (mx > 0x1p+256 || (mx > 0.0 && mx < 0x1p-256)) {
+    const double s = pow2_near_inverse(mx);
+    C.m00 = dd_scale(C.m00, s); C.m01 = dd_scale(C.m01, s);
+    C.m10 = dd_scale(C.m10, s); C.m11 = dd_scale(C.m11, s);
+  }
+}
+
+constexpr int kPivotThreads = 256;
+
+__global__ void __launch_bounds__(kPivotThreads) k_pivots(const double* __restrict__ a, const double* __restrict__ b,
+                                                          int64_t n, dd* __restrict__ dF, dd* __restrict__ dB,
+                                                          unsigned long long* stat) {
+  __shared__ dd2x2 chunk[kPivotThreads];
+  __shared__ dd sp[kPivotThreads], sq[kPivotThreads];
+  const bool fwd = blockIdx.x == 0;
+  const int T = blockDim.x, t = threadIdx.x;
   const double normA = __longlong_as_double((long long)stat[1]);
   const double tiny = 64.0 * 1.1102230246251565e-16 * normA;
-  double dmin = INFINITY;
-  if (threadIdx.x == 0) {
-    dd d = dd_make(b[0]);
-    dF[0] = d;
-    dmin = fabs(d.hi);
-    for (int64_t i = 1; i < n; i++) {
-      if (d.hi == 0.0) break;
-      d = dd_sub(dd_make(b[i]), dd_div(two_prod(a[i - 1], a[i - 1]), d));
-      dF[i] = d;
-      dmin = fmin(dmin, fabs(d.hi));
-    }
-  } else if (threadIdx.x == 1) {
-    dd d = dd_make(b[n - 1]);
-    dB[n - 1] = d;
-    dmin = fabs(d.hi);
-    for (int64_t i = n - 2; i >= 0; i--) {
-      if (d.hi == 0.0) break;
-      d = dd_sub(dd_make(b[i]), dd_div(two_prod(a[i], a[i]), d));
-      dB[i] = d;
-      dmin = fmin(dmin, fabs(d.hi));
-    }
-  } else {
-    return;
+  // step k (0 .. n-2) produces the pivot of row fwd ? k + 1 : n - 2 - k with a = a[fwd ? k : n - 2 - k]
+  const int64_t steps = n - 1;
+  const int64_t Q = (steps + T - 1) / T;
+  const int64_t k0 = (int64_t)t * Q < steps ? (int64_t)t * Q : steps;
+  const int64_t k1 = k0 + Q < steps ? k0 + Q : steps;
+  dd2x2 C{dd_make(1.0), dd_make(0.0), dd_make(0.0), dd_make(1.0)};
+  for (int64_t k = k0; k < k1; k++) {
+    const int64_t ia = fwd ? k : n - 2 - k;
+    mob_step(C, b[fwd ? k + 1 : n - 2 - k], two_prod(a[ia], a[ia]));
+    if ((k - k0) % 16 == 15) mob_rescale(C);
   }
-  if (!(dmin > tiny) || !isfinite(dmin)) atomicOr(&stat[0], (unsigned long long)kStatSingular);
-  atomic_min_pos(&stat[2], isfinite(dmin) ? dmin : 0.0);
+  mob_rescale(C);
+  chunk[t] = C;
+  __syncthreads();
+  if (t == 0) {   // the state entering every chunk
+    dd p = dd_make(b[fwd ? 0 : n - 1]), q = dd_make(1.0);
+    for (int u = 0; u < T; u++) {
+      sp[u] = p;
+      sq[u] = q;
+      const dd2x2 M = chunk[u];
+      const dd np = dd_add(dd_mul(M.m00, p), dd_mul(M.m01, q));
+      const dd nq = dd_add(dd_mul(M.m10, p), dd_mul(M.m11, q));
+      const double mx = fmax(fabs(np.hi), fabs(nq.hi));
+      const double sc = (mx > 0x1p+256 || (mx > 0.0 && mx < 0x1p-256)) ? pow2_near_inverse(mx) : 1.0;
+      p = dd_scale(np, sc);
+      q = dd_scale(nq, sc);
+    }
+  }
+  __syncthreads();
+  double dmin = INFINITY;
+  bool bad = false;
+  dd* out = fwd ? dF : dB;
+  if (t == 0) {
+    const double d0 = b[fwd ? 0 : n - 1];
+    out[fwd ? 0 : n - 1] = dd_make(d0);
+    dmin = fabs(d0);
+    bad = !isfinite(d0);
+  }
+  if (k0 < k1) {
+    dd d = dd_div(sp[t], sq[t]);   // the pivot of the row before the chunk
+    for (int64_t k = k0; k < k1; k++) {
+      const int64_t ia = fwd ? k : n - 2 - k;
+      const int64_t row = fwd ? k + 1 : n - 2 - k;
+      d = dd_sub(dd_make(b[row]), dd_div(two_prod(a[ia], a[ia]), d));
+      out[row] = d;
+      if (!isfinite(d.hi)) bad = true;
+      else dmin = fmin(dmin, fabs(d.hi));
+    }
+  }
+  if (bad || !(dmin > tiny)) atomicOr(&stat[0], (unsigned long long)kStatSingular);
+  if (dmin < INFINITY) atomic_min_pos(&stat[2], dmin);
 }
 
 template <typename T>
@@ -384,7 +449,7 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
   if (e == cudaSuccess) e = cudaMemsetAsync(p->dev_err, 0, sizeof(int), s);
   if (e == cudaSuccess) {
     k_norm_and_dominance<<<64, 256, 0, s>>>(p->a64, p->b64, n, p->stat);
-    k_pivots<<<1, 32, 0, s>>>(p->a64, p->b64, n, reinterpret_cast<dd*>(p->piv), reinterpret_cast<dd*>(p->piv) + n, p->stat);
+    k_pivots<<<2, kPivotThreads, 0, s>>>(p->a64, p->b64, n, reinterpret_cast<dd*>(p->piv), reinterpret_cast<dd*>(p->piv) + n, p->stat);
     k_block_coefficients<<<(p->M + 127) / 128, 128, 0, s>>>(
         p->a64, p->b64, n, t, p->M, reinterpret_cast<dd*>(p->piv), reinterpret_cast<dd*>(p->piv) + n, p->coef64, p->coef32, p->rR, p->rL, p->stat);
     k_residual_coefficients<<<(int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, s>>>(
