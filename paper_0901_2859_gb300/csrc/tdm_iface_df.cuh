@@ -43,13 +43,14 @@ struct IfaceOffsets {
   size_t tmp;        // double [96] set-up scratch
   size_t bytes;
 };
-__host__ __device__ constexpr IfaceOffsets iface_offsets(int R, int MM) {
+__host__ __device__ constexpr IfaceOffsets iface_offsets(int R, int MM, bool pair) {
+  const size_t es = pair ? 8 : 4;   // LR, LL: pairs, or the leading words only
   IfaceOffsets o{};
   size_t p = 0;
   o.beR = p; p += round16(4 * (size_t)MM * (R + 1));
   o.beL = p; p += round16(4 * (size_t)MM * (R + 1));
-  o.lr = p; p += round16(8 * (size_t)(MM + 1) * (R + 1));
-  o.ll = p; p += round16(8 * (size_t)(MM + 1) * (R + 1));
+  o.lr = p; p += round16(es * (size_t)(MM + 1) * (R + 1));
+  o.ll = p; p += round16(es * (size_t)(MM + 1) * (R + 1));
   o.aR = p; p += round16(8 * (size_t)MM);
   o.aL = p; p += round16(8 * (size_t)MM);
   o.cpR = p; p += round16(8 * (size_t)MM);
@@ -69,9 +70,9 @@ __host__ __device__ constexpr IfaceOffsets iface_offsets(int R, int MM) {
 
 // The arrays at compile-time offsets from `base` (16-byte aligned shared
 // memory), so that every access is an immediate offset.
-template <int R, int MM>
+template <int R, int MM, bool PAIR = true>
 struct IfaceDF {
-  static constexpr IfaceOffsets O = iface_offsets(R, MM);
+  static constexpr IfaceOffsets O = iface_offsets(R, MM, PAIR);
   // Row stride of beR, beL, lr, ll: the scan reads them down a column (lane =
   // block), the blocks write and read them along a row; one padding entry per
   // row keeps both directions free of bank conflicts.
@@ -79,8 +80,23 @@ struct IfaceDF {
   unsigned char* base;
   __device__ float* beR() const { return reinterpret_cast<float*>(base + O.beR); }
   __device__ float* beL() const { return reinterpret_cast<float*>(base + O.beL); }
-  __device__ float2* lr() const { return reinterpret_cast<float2*>(base + O.lr); }
-  __device__ float2* ll() const { return reinterpret_cast<float2*>(base + O.ll); }
+  // LR_j, LL_j entries: pairs (PAIR) or their leading words
+  __device__ f2pair ld_lr(int k) const { return ld_entry(O.lr, k); }
+  __device__ f2pair ld_ll(int k) const { return ld_entry(O.ll, k); }
+  __device__ void st_lr(int k, f2pair v) const { st_entry(O.lr, k, v); }
+  __device__ void st_ll(int k, f2pair v) const { st_entry(O.ll, k, v); }
+  __device__ f2pair ld_entry(size_t off, int k) const {
+    if constexpr (PAIR) {
+      const float2 v = reinterpret_cast<const float2*>(base + off)[k];
+      return f2pair{v.x, v.y};
+    } else {
+      return f2pair{reinterpret_cast<const float*>(base + off)[k], 0.f};
+    }
+  }
+  __device__ void st_entry(size_t off, int k, f2pair v) const {
+    if constexpr (PAIR) reinterpret_cast<float2*>(base + off)[k] = make_float2(v.h, v.l);
+    else reinterpret_cast<float*>(base + off)[k] = v.h;
+  }
   __device__ float2* aR() const { return reinterpret_cast<float2*>(base + O.aR); }
   __device__ float2* aL() const { return reinterpret_cast<float2*>(base + O.aL); }
   __device__ float2* cpR() const { return reinterpret_cast<float2*>(base + O.cpR); }
@@ -171,8 +187,8 @@ __device__ __forceinline__ float2 ld_cluster_f32x2(const float2* local, unsigned
 // Per-series set-up of every product (binary64, then pairs).  All threads of
 // the CTA call it; it synchronizes the CTA.  rR, rL have M + 2 entries; the
 // multipliers of CTA c are aR_j = rR[c m + j], aL_j = rL[c m + j + 1].
-template <int R, int MM>
-__device__ __forceinline__ void iface_df_setup(const IfaceDF<R, MM>& f, const double* rR, const double* rL, int M,
+template <int R, int MM, bool PAIR>
+__device__ __forceinline__ void iface_df_setup(const IfaceDF<R, MM, PAIR>& f, const double* rR, const double* rL, int M,
                                                int m, int C, unsigned c) {
   const int tid = threadIdx.x, nt = blockDim.x;
   auto gR = [&](int q) -> double { return (q >= 0 && q <= M + 1) ? rR[q] : 0.0; };
@@ -243,8 +259,8 @@ __device__ __forceinline__ void iface_df_setup(const IfaceDF<R, MM>& f, const do
 // LR_j, LL_j of this CTA and its totals (into xch[parity]); one warp scans a
 // column in both directions.  The betas must be visible (CTA barrier).
 template <int R, int MM, bool PAIR = true>
-__device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM>& f, int m, int parity) {
-  constexpr int RP = IfaceDF<R, MM>::kRP;
+__device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM, PAIR>& f, int m, int parity) {
+  constexpr int RP = IfaceDF<R, MM, PAIR>::kRP;
   constexpr int KMAX = (MM + 31) / 32;   // most blocks per lane (1: every lane holds one block)
   const int lane = threadIdx.x & 31;
   const int K = KMAX == 1 ? 1 : (m + 31) / 32, nl = (m + K - 1) / K;
@@ -254,11 +270,11 @@ __device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM>& f, int m, in
     f2pair accR{0.f, 0.f}, accL{0.f, 0.f};
     for (int j = j0; j < j1; j++) {
       accR = mfma<PAIR>(mld<PAIR>(&f.aR()[j]), accR, f2pair{f.beR()[j * RP + r], 0.f});
-      if (KMAX > 1 && K > 1) f.lr()[(j + 1) * RP + r] = f2(accR);
+      if (KMAX > 1 && K > 1) f.st_lr((j + 1) * RP + r, accR);
     }
     for (int j = j1 - 1; j >= j0; j--) {
       accL = mfma<PAIR>(mld<PAIR>(&f.aL()[j]), accL, f2pair{f.beL()[j * RP + r], 0.f});
-      if (KMAX > 1 && K > 1) f.ll()[j * RP + r] = f2(accL);
+      if (KMAX > 1 && K > 1) f.st_ll(j * RP + r, accL);
     }
 #pragma unroll
     for (int l = 0; l < 5; l++) {
@@ -274,21 +290,21 @@ __device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM>& f, int m, in
       if (lane == 0) eR = f2pair{0.f, 0.f};
       if (lane + 1 >= nl) eL = f2pair{0.f, 0.f};
       for (int j = j0; j < j1; j++) {
-        f.lr()[(j + 1) * RP + r] = f2(mfma<PAIR>(mld<PAIR>(&f.cpR()[j]), eR, mld<PAIR>(&f.lr()[(j + 1) * RP + r])));
-        f.ll()[j * RP + r] = f2(mfma<PAIR>(mld<PAIR>(&f.cpL()[j]), eL, mld<PAIR>(&f.ll()[j * RP + r])));
+        f.st_lr((j + 1) * RP + r, mfma<PAIR>(mld<PAIR>(&f.cpR()[j]), eR, f.ld_lr((j + 1) * RP + r)));
+        f.st_ll(j * RP + r, mfma<PAIR>(mld<PAIR>(&f.cpL()[j]), eL, f.ld_ll(j * RP + r)));
       }
     } else if (j0 < m) {   // one block per lane: the scan already holds the values
-      f.lr()[(j0 + 1) * RP + r] = f2(accR);
-      f.ll()[j0 * RP + r] = f2(accL);
+      f.st_lr((j0 + 1) * RP + r, accR);
+      f.st_ll(j0 * RP + r, accL);
     }
     if (lane == 0) {
-      f.lr()[r] = make_float2(0.f, 0.f);
-      f.ll()[m * RP + r] = make_float2(0.f, 0.f);
+      f.st_lr(r, f2pair{0.f, 0.f});
+      f.st_ll(m * RP + r, f2pair{0.f, 0.f});
     }
     __syncwarp();
     if (lane == 0) {
-      f.xch()[(parity * 2 + 0) * R + r] = f.lr()[m * RP + r];
-      f.xch()[(parity * 2 + 1) * R + r] = f.ll()[r];
+      f.xch()[(parity * 2 + 0) * R + r] = f2(f.ld_lr(m * RP + r));
+      f.xch()[(parity * 2 + 1) * R + r] = f2(f.ld_ll(r));
     }
   }
 }
@@ -297,7 +313,7 @@ __device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM>& f, int m, in
 // barrier): one warp per column, lanes 0-15 for the CTAs to the left, 16-31
 // for those to the right.
 template <int R, int MM, bool PAIR = true>
-__device__ __forceinline__ void iface_df_fold(const IfaceDF<R, MM>& f, int C, unsigned c, int parity) {
+__device__ __forceinline__ void iface_df_fold(const IfaceDF<R, MM, PAIR>& f, int C, unsigned c, int parity) {
   const int lane = threadIdx.x & 31, cc = lane & 15;
   const bool left = lane < 16;
   const bool valid = left ? (cc < (int)c) : (cc > (int)c && cc < C);
@@ -316,9 +332,9 @@ __device__ __forceinline__ void iface_df_fold(const IfaceDF<R, MM>& f, int C, un
 
 // x(p_j) for column r, rounded to binary32
 template <int R, int MM, bool PAIR = true>
-__device__ __forceinline__ float iface_df_sep(const IfaceDF<R, MM>& f, int j, int r) {
-  constexpr int RP = IfaceDF<R, MM>::kRP;
-  f2pair x = madd<PAIR>(mld<PAIR>(&f.lr()[j * RP + r]), mld<PAIR>(&f.ll()[j * RP + r]));
+__device__ __forceinline__ float iface_df_sep(const IfaceDF<R, MM, PAIR>& f, int j, int r) {
+  constexpr int RP = IfaceDF<R, MM, PAIR>::kRP;
+  f2pair x = madd<PAIR>(f.ld_lr(j * RP + r), f.ld_ll(j * RP + r));
   x = mfma<PAIR>(mld<PAIR>(&f.piR()[j]), mld<PAIR>(&f.in()[r]), x);
   x = mfma<PAIR>(mld<PAIR>(&f.piL()[j]), mld<PAIR>(&f.in()[R + r]), x);
   return x.h + x.l;

@@ -23,6 +23,15 @@ __device__ __forceinline__ void cluster_barrier() {
   __syncthreads();
   if (threadIdx.x >= 32) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// The two halves of a cluster barrier, for work that overlaps its completion:
+// arrive after the writes the other CTAs will read (release), wait before
+// reading theirs (acquire).  Every thread of every CTA executes both.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 // load a double from the same shared-memory offset in CTA `rank` of the cluster
 __device__ __forceinline__ double ld_cluster_f64(const double* local, unsigned rank) {
   const unsigned laddr = (unsigned)__cvta_generic_to_shared(local);
@@ -249,6 +258,35 @@ __device__ __forceinline__ void forward_pass(T (&v)[TT], const T* cf, int nrows,
       g = fma(-lf, g, v[i]);
       v[i] = g;
     }
+  }
+}
+
+// A5 of the plain solve in two parts: the back substitution (independent of
+// the separator values, y replaces v), then the correction with the two
+// separator values and the store of each row; p points at the block's first
+// row of X.
+template <typename T, int TT, bool FULL>
+__device__ __forceinline__ void backward_y_plain(T (&v)[TT], const T* cf, int nrows) {
+  T y = T(0);
+#pragma unroll
+  for (int i = TT - 1; i >= 0; i--) {
+    if (FULL || i < nrows) {
+      const T cc = cf[i * kNCOEF + kC], invd = cf[i * kNCOEF + kINVD];
+      y = fma(-cc, y, v[i]) * invd;
+      v[i] = y;
+    }
+  }
+}
+template <typename T, int TT, bool FULL>
+__device__ __forceinline__ void correct_store(const T (&v)[TT], const T* cf, int nrows, T xL, T xR, T* p, int64_t ld,
+                                              bool col_ok) {
+#pragma unroll
+  for (int i = 0; i < TT; i++) {
+    if (FULL || i < nrows) {
+      const T x = fma(cf[i * kNCOEF + kPHIR], xR, fma(cf[i * kNCOEF + kPHIL], xL, v[i]));
+      if (col_ok) *p = x;
+    }
+    p += ld;
   }
 }
 

@@ -110,16 +110,6 @@ __device__ __forceinline__ void cta_maxima(float md, float mx, float* red, float
   }
 }
 
-// The two halves of a cluster barrier, for work that overlaps its completion:
-// arrive after the writes the other CTAs will read (release), wait before
-// reading theirs (acquire).  Every thread of every CTA executes both.
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 // streaming loads/stores for the right-hand sides and the solution: they are
 // touched once per tile and must not evict the coefficients from L1
 __device__ __forceinline__ float ld_stream(const float* p) {
@@ -329,7 +319,7 @@ __host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, b
   o.coef = p; if (sm_coef) p += round16(4 * MM * (TT * kNCOEF + 4));
   o.res = p; if (sm_coef) p += round16(16 * MM * (TT + 1));
   o.pad = p; if (sm_coef) p += round16(4 * (size_t)(TT + 1) * R);   // delta words of threads past the blocks
-  o.iface = p; p += iface_offsets(R, (int)MM).bytes;
+  o.iface = p; p += iface_offsets(R, (int)MM, true).bytes;
   o.bytes = p;
   return o;
 }

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
   unsigned char* const a4 = reinterpret_cast<unsigned char*>(scf) + coef_bytes(a.m, TT, (int)sizeof(T));
   const Smem s = carve(a4, a.m, R, (int)sizeof(T));
   constexpr int MM = MAXT / R;
-  const IfaceDF<R, MM> f{a4};
+  const IfaceDF<R, MM, false> f{a4};
   const unsigned c = cluster_rank();
   const int tid = threadIdx.x;
   const int r = tid % R;
@@ -183,13 +183,21 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
       }
       __syncthreads();
       iface_df_scan<R, MM, false>(f, a.m, parity);
-      cluster_barrier();
+      cluster_arrive();   // the back substitution overlaps the exchange of the CTA totals
+      if (nrows == TT) backward_y_plain<T, TT, true>(v, cfb, nrows);
+      else backward_y_plain<T, TT, false>(v, cfb, nrows);
+      cluster_wait();
       iface_df_fold<R, MM, false>(f, a.C, c, parity);
       __syncthreads();
       if (blk_ok) {
         if (b >= 1) xL = iface_df_sep<R, MM, false>(f, bl, r);
         if (b + 1 <= a.M - 1) xR = iface_df_sep<R, MM, false>(f, bl + 1, r);
       }
+      T* Xp = X + row0 * a.ldX + col;
+      if (nrows == TT) correct_store<T, TT, true>(v, cfb, nrows, xL, xR, Xp, a.ldX, col_ok);
+      else correct_store<T, TT, false>(v, cfb, nrows, xL, xR, Xp, a.ldX, col_ok);
+      parity ^= 1;
+      continue;
     }
     // A5: back substitution + correction + store
     T* Xp = X + row0 * a.ldX + col;
@@ -315,7 +323,7 @@ tdm_status tdm_launch_plain(tdm_plan_s* p, const void* F, int64_t ldF, void* X, 
   auto bytes = [&](bool tma) {
     return fp64 ? smem_bytes(cfg.m, p->t, cfg.R, tsize, tma)
                 : 128 + fbuf_bytes(cfg.m, p->t, cfg.R, tsize, tma) + coef_bytes(cfg.m, p->t, tsize) +
-                      iface_offsets(cfg.R, 512 / cfg.R).bytes;
+                      iface_offsets(cfg.R, 512 / cfg.R, false).bytes;
   };
   cfg.smem = bytes(cfg.tma);
   if (cfg.smem > 227 * 1024) {   // fall back to direct loads when the staging buffer does not fit
