@@ -641,15 +641,17 @@ tdm_status launch_shape(const RefShape& sh, const RefLaunch& L, int nitems, cuda
 //           CTA (n <= 16384); R = 4 with 512 threads (2048 rows) or 1024
 //           threads (4096 rows, n <= 65536), coefficients read through L1.
 //   t = 32: R = 8, 256 threads, two CTAs per SM (128 registers, n <= 16384);
-//           R = 4, 512 threads (n <= 65536); R = 16, 512 threads on request.
+//           R = 8, 512 threads, one CTA per SM (n <= 32768); R = 4, 512
+//           threads, coefficients read through L1 (n <= 65536); R = 16,
+//           512 threads on request.
 bool tdm_refined_shape(int M, int t, RefShape& sh) {
   const char* env = getenv("TDM_REFINE_R");
   const int pref = env ? atoi(env) : 8;
   struct Cand { int R, NT; bool sm; };
-  const Cand c16[3] = {{8, 512, true}, {4, 512, false}, {4, 1024, false}};
-  const Cand c32[3] = {{pref, pref == 8 ? 256 : 512, pref != 4}, {8, 256, true}, {4, 512, false}};
+  const Cand c16[4] = {{8, 512, true}, {4, 512, false}, {4, 1024, false}, {4, 1024, false}};
+  const Cand c32[4] = {{pref, pref == 8 ? 256 : 512, pref != 4}, {8, 256, true}, {8, 512, true}, {4, 512, false}};
   const Cand* cand = t == 16 ? c16 : c32;
-  for (int k = 0; k < 3; k++) {
+  for (int k = 0; k < 4; k++) {
     const int R = cand[k].R, NT = cand[k].NT;
     if (R != 4 && R != 8 && R != 16) continue;
     const int m_max = NT / R;
@@ -682,6 +684,7 @@ tdm_status tdm_refined_launch(const RefShape& sh, int t, const RefItem* items, c
   const int key = sh.R * 100000 + sh.NT * 10 + (t == 16 ? 1 : 0);
   switch (key) {
     case 8 * 100000 + 256 * 10 + 0: return launch_shape<8, 32, 256, 2, true>(sh, L, nitems, s);
+    case 8 * 100000 + 512 * 10 + 0: return launch_shape<8, 32, 512, 1, true>(sh, L, nitems, s);
     case 4 * 100000 + 512 * 10 + 0: return launch_shape<4, 32, 512, 1, false>(sh, L, nitems, s);
     case 16 * 100000 + 512 * 10 + 0: return launch_shape<16, 32, 512, 1, true>(sh, L, nitems, s);
     case 8 * 100000 + 512 * 10 + 1: return launch_shape<8, 16, 512, 2, true>(sh, L, nitems, s);
