@@ -326,7 +326,6 @@ def run_batching(args):
                    "matrices": len(specs), "unknowns": unknowns, "refine_steps": steps_used},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "peak_source": peak_kind, "kernel": "k_refined"},
-        "gpu_launches": args.steps,
         "paths": {"one_launch_ms": ms_batched, "graph_replay_ms": ms_graph, "per_matrix_loop_ms": ms_loop,
                   "speedup_vs_loop": ms_loop / ms_batched},
         "prepare_s_all_matrices": prepare_s,
