@@ -87,7 +87,9 @@ typedef struct {
                               large to calibrate cheaply (n > ~350000 uses fewer columns,
                               n > ~2.8e6 none).  tdm_info reports the result. */
   int flags;         /* reserved, must be 0 */
-  int reserved;
+  int tile_rhs;      /* TDM_FP32_REFINED: right-hand sides per tile of the solve kernel, 4, 8 or
+                        16; 0 (automatic) = 8 where the shape fits (the shape rule falls back to
+                        other widths when a requested one does not fit the system size) */
 } tdm_options;
 
 typedef struct {
@@ -102,7 +104,7 @@ typedef struct {
   int32_t device_error;    /* device-side error code of the last solves (0 = none,
                               1 = a TMA transfer timed out, 2 = refinement cap reached
                               before the convergence test passed) */
-  int32_t reserved;
+  int32_t tile_rhs;        /* the plan's tile_rhs option (0 = automatic) */
 } tdm_info;
 
 /* tdm_prepare -- Algorithm 3/4, step 1 (Sections 3.3-3.4; eqs. green_v, z_vector).

@@ -9,5 +9,6 @@ with a correction), all as CUDA kernels for sm_103a behind the C ABI in
 """
 from .api import Plan, TDMError, TDMSolve, prepare, solve_batched, solve_batched_noalloc, tdm_solve  # noqa: F401
 from ._build import build  # noqa: F401
+from . import autotune  # noqa: F401
 
 __all__ = ["Plan", "TDMError", "TDMSolve", "prepare", "solve_batched", "solve_batched_noalloc", "tdm_solve", "build"]

@@ -23,14 +23,14 @@ NOALLOC_MAX_TILES = 4096   # TDM_NOALLOC_MAX_TILES
 
 class TDMOptions(ctypes.Structure):
     _fields_ = [("block_rows", ctypes.c_int), ("refine_steps", ctypes.c_int),
-                ("flags", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("tile_rhs", ctypes.c_int)]
 
 
 class TDMInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("block_rows", ctypes.c_int32), ("num_blocks", ctypes.c_int32),
                 ("dominant", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("max_abs_z", ctypes.c_double), ("min_abs_pivot", ctypes.c_double),
-                ("device_error", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("device_error", ctypes.c_int32), ("tile_rhs", ctypes.c_int32)]
 
 
 class TDMError(RuntimeError):

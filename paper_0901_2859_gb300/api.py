@@ -39,7 +39,8 @@ def _check_rhs(T: torch.Tensor, n: int, dtype: torch.dtype, name: str) -> int:
 class Plan:
     """A prepared matrix (Algorithm 3/4 step 1).  Owns device memory until closed."""
 
-    def __init__(self, a: torch.Tensor, b: torch.Tensor, block_rows: int = 0, refine_steps: int = 0):
+    def __init__(self, a: torch.Tensor, b: torch.Tensor, block_rows: int = 0, refine_steps: int = 0,
+                 tile_rhs: int = 0):
         lib = _lib.load()
         if not (isinstance(b, torch.Tensor) and b.is_cuda):
             raise TypeError("a and b must be CUDA tensors (float64)")
@@ -50,7 +51,7 @@ class Plan:
             raise ValueError(f"a must have n-1 = {n - 1} entries, got {a.numel()}")
         self.device = b.device
         self.n = n
-        opts = TDMOptions(block_rows, refine_steps, 0, 0)
+        opts = TDMOptions(block_rows, refine_steps, 0, tile_rhs)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = lib.tdm_prepare(ctypes.c_void_p(a.data_ptr() if n > 1 else 0), ctypes.c_void_p(b.data_ptr()),
@@ -68,7 +69,7 @@ class Plan:
     def info(self) -> dict:
         inf = TDMInfo()
         check(_lib.load().tdm_get_info(self.handle, ctypes.byref(inf)), "tdm_get_info")
-        return {f: getattr(inf, f) for f, _ in TDMInfo._fields_ if f != "reserved"}
+        return {f: getattr(inf, f) for f, _ in TDMInfo._fields_}
 
     def solve(self, F: torch.Tensor, precision: str = "fp32", out: torch.Tensor | None = None) -> torch.Tensor:
         """X = A^{-1} F for every column of F (shape (n, N), right-hand sides contiguous)."""
@@ -128,13 +129,13 @@ class Plan:
         self.close()
 
 
-def prepare(a, b, block_rows: int = 0, refine_steps: int = 0, device=None) -> Plan:
+def prepare(a, b, block_rows: int = 0, refine_steps: int = 0, device=None, tile_rhs: int = 0) -> Plan:
     """Prepare A = tridiag(a, b, a); a, b may be CUDA tensors or host arrays."""
     if not isinstance(b, torch.Tensor) or not b.is_cuda:
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         b = torch.as_tensor(b, dtype=torch.float64).to(dev)
         a = torch.as_tensor(a, dtype=torch.float64).to(dev)
-    return Plan(a, b, block_rows=block_rows, refine_steps=refine_steps)
+    return Plan(a, b, block_rows=block_rows, refine_steps=refine_steps, tile_rhs=tile_rhs)
 
 
 def solve_batched(plans, Fs, precision: str = "fp32_refined", outs=None):

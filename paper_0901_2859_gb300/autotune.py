@@ -1,0 +1,128 @@
+"""Measured choice of a matrix's solve configuration.
+
+Two parameters shape the solve kernels:
+
+* ``block_rows``: rows per block, 16 or 32. This is the size of the paper's
+  subvectors, and it fixes M and the length of the separator recurrences.
+* ``tile_rhs``: right-hand sides per tile of the refined kernel, 4, 8 or 16.
+  It fixes how many blocks a CTA owns and the cluster size.
+
+``tune`` times every valid combination on a sample block of right-hand sides
+with CUDA events and keeps the fastest. It caches the choice per (device,
+n, precision) in a JSON file: ``$TDM_TUNE_CACHE``, else
+``~/.cache/tdm/autotune.json``. ``prepare_tuned`` prepares a plan with the
+cached or measured choice. The library's own rule (32 rows, 8 right-hand
+sides where the shape fits) is the default without tuning.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+import torch
+
+from .api import TDMError, prepare
+
+__all__ = ["CANDIDATES", "PLAIN_CANDIDATES", "cache_path", "tune", "prepare_tuned", "select"]
+
+# (block_rows, tile_rhs); tile_rhs only changes the refined kernel
+CANDIDATES = ((32, 8), (32, 16), (32, 4), (16, 8), (16, 4))
+PLAIN_CANDIDATES = ((32, 0), (16, 0))
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("TDM_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "tdm", "autotune.json")
+
+
+def _key(device_name: str, n: int, precision: str) -> str:
+    return f"{device_name}|n={n}|{precision}"
+
+
+def _read(path: str) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _write(path: str, data: dict) -> None:
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def select(candidates, measure):
+    """The candidate with the smallest measured time. measure(c) returns a time,
+    or None when the configuration does not apply (e.g. does not fit the size)."""
+    times = {}
+    for c in candidates:
+        t = measure(c)
+        if t is not None:
+            times[c] = float(t)
+    if not times:
+        raise ValueError("no candidate configuration applies")
+    best = min(times, key=lambda c: (times[c], candidates.index(c)))
+    return best, times
+
+
+def _measure(a, b, dev, precision, block_rows, tile_rhs, sample_rhs, reps):
+    try:
+        plan = prepare(a, b, block_rows=block_rows, tile_rhs=tile_rhs, device=dev)
+    except TDMError:
+        return None
+    try:
+        n = plan.n
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(n)
+        dt_in = torch.float64 if precision == "fp64" else torch.float32
+        F = torch.randn((n, sample_rhs), device=dev, generator=gen, dtype=torch.float32).to(dt_in)
+        X = torch.empty((n, sample_rhs), device=dev, dtype=torch.float32 if precision == "fp32" else torch.float64)
+        plan.solve(F, precision, out=X)   # warm-up (and first-use set-up)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            plan.solve(F, precision, out=X)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+    except TDMError:
+        return None
+    finally:
+        plan.close()
+
+
+def tune(a, b, precision: str = "fp32_refined", device=None, sample_rhs: int = 2048, reps: int = 3,
+         use_cache: bool = True, candidates=None) -> dict:
+    """{'block_rows', 'tile_rhs', 'ms', 'candidates'} for the matrix (a, b)."""
+    if candidates is None:
+        candidates = CANDIDATES if precision == "fp32_refined" else PLAIN_CANDIDATES
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    n = int(len(b))
+    key = _key(torch.cuda.get_device_name(dev), n, precision)
+    path = cache_path()
+    with _lock:
+        if use_cache:
+            hit = _read(path).get(key)
+            if hit:
+                return hit
+        best, times = select(list(candidates),
+                             lambda c: _measure(a, b, dev, precision, c[0], c[1], sample_rhs, reps))
+        entry = {"block_rows": best[0], "tile_rhs": best[1], "ms": times[best], "sample_rhs": sample_rhs,
+                 "candidates": {f"{c[0]}x{c[1]}": t for c, t in times.items()}}
+        if use_cache:
+            data = _read(path)
+            data[key] = entry
+            _write(path, data)
+        return entry
+
+
+def prepare_tuned(a, b, precision: str = "fp32_refined", device=None, **tune_kw):
+    """prepare() with the tuned block_rows and tile_rhs of this size."""
+    cfg = tune(a, b, precision=precision, device=device, **tune_kw)
+    return prepare(a, b, block_rows=cfg["block_rows"], tile_rhs=cfg["tile_rhs"], device=device)

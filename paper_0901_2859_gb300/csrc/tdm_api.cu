@@ -207,6 +207,7 @@ extern "C" tdm_status tdm_get_info(tdm_handle h, tdm_info* info) {
   info->max_abs_z = h->max_abs_z;
   info->min_abs_pivot = h->min_abs_pivot;
   info->device_error = err;
+  info->tile_rhs = h->tile_rhs;
   return TDM_OK;
 }
 

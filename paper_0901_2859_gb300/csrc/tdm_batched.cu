@@ -71,7 +71,7 @@ tdm_status build(WorkList* w, tdm_plan_s* const* ps, int count, const void* cons
   for (int k = 0; k < count; k++) {
     if (N[k] == 0) continue;
     RefShape sh;
-    if (!tdm_refined_shape(ps[k]->M, ps[k]->t, sh)) return TDM_ERR_NOT_IMPLEMENTED;
+    if (!tdm_refined_shape(ps[k]->M, ps[k]->t, ps[k]->tile_rhs, sh)) return TDM_ERR_NOT_IMPLEMENTED;
     es.push_back({k, sh, (double)ps[k]->n * (double)N[k]});
   }
   auto same = [](const RefShape& a, const RefShape& b) {

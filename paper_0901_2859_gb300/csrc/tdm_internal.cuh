@@ -43,7 +43,8 @@ struct tdm_plan_s {
   int64_t n = 0;
   int t = 0;               // rows per block
   int M = 0;               // number of blocks, M - 1 separators
-  int refine_steps = 0;      // 0: adaptive (cap 4); k > 0: exactly k corrections
+  int refine_steps = 0;      // -1: tested per tile (cap 4); k > 0: exactly k corrections
+  int tile_rhs = 0;          // right-hand sides per refined tile (0: by the shape rule)
   int dominant = 0;
   double max_abs_z = 0.0;
   double min_abs_pivot = 0.0;

@@ -114,7 +114,7 @@ extern "C" tdm_status tdm_solve_batched_noalloc(const tdm_handle* hs, int count,
     Entry e;
     e.k = k;
     e.t = hs[k]->t;
-    if (!tdm_refined_shape(hs[k]->M, e.t, e.sh)) return TDM_ERR_NOT_IMPLEMENTED;
+    if (!tdm_refined_shape(hs[k]->M, e.t, hs[k]->tile_rhs, e.sh)) return TDM_ERR_NOT_IMPLEMENTED;
     const int64_t tiles = (N[k] + e.sh.R - 1) / e.sh.R;
     total += tiles;
     if (total > kMaxTiles) return TDM_ERR_TOO_LARGE;

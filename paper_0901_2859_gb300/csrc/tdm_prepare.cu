@@ -366,7 +366,7 @@ tdm_status calibrate_refinement(tdm_plan_s* p, cudaStream_t s) {
   while (N > 8 && (size_t)p->n * N * 12 > kCalibBytes) N /= 2;
   if ((size_t)p->n * N * 12 > kCalibBytes) return TDM_OK;
   RefShape sh;
-  if (!tdm_refined_shape(p->M, p->t, sh)) return TDM_OK;
+  if (!tdm_refined_shape(p->M, p->t, p->tile_rhs, sh)) return TDM_OK;
   float* F = nullptr;
   double* X = nullptr;
   tdm_status st = TDM_OK;
@@ -402,14 +402,16 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
   *out = nullptr;
   if (n < 1 || n > (int64_t(1) << 26) || !b || (n > 1 && !a)) return TDM_ERR_INVALID_ARG;
   if (!tdm_aligned(b, 8) || (a && !tdm_aligned(a, 8))) return TDM_ERR_INVALID_ARG;
-  int t = 32, steps = 0;
+  int t = 32, steps = 0, tile = 0;
   if (opt) {
     if (opt->flags != 0) return TDM_ERR_INVALID_ARG;
     if (opt->block_rows != 0) t = opt->block_rows;
+    tile = opt->tile_rhs;
     if (opt->refine_steps != 0) steps = opt->refine_steps;
   }
   if (t != 16 && t != 32) return TDM_ERR_INVALID_ARG;
   if (steps < -1 || steps > 4) return TDM_ERR_INVALID_ARG;
+  if (tile != 0 && tile != 4 && tile != 8 && tile != 16) return TDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   (void)cudaGetLastError();   // report only errors of this call
 
@@ -418,6 +420,7 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
   p->t = t;
   p->M = (int)((n + t - 1) / t);
   p->refine_steps = steps;
+  p->tile_rhs = tile;
   cudaGetDevice(&p->device);
   const int64_t na = n > 1 ? n - 1 : 1;
   bool ok = cudaMalloc(&p->coef64, sizeof(double) * n * kNCOEF) == cudaSuccess &&

@@ -644,15 +644,18 @@ tdm_status launch_shape(const RefShape& sh, const RefLaunch& L, int nitems, cuda
 //           R = 8, 512 threads, one CTA per SM (n <= 32768); R = 4, 512
 //           threads, coefficients read through L1 (n <= 65536); R = 16,
 //           512 threads on request.
-bool tdm_refined_shape(int M, int t, RefShape& sh) {
-  const char* env = getenv("TDM_REFINE_R");
-  const int pref = env ? atoi(env) : 8;
+// A requested width (pref) is tried first; the rule's shapes follow.
+bool tdm_refined_shape(int M, int t, int pref, RefShape& sh) {
   struct Cand { int R, NT; bool sm; };
+  // the requested width first (16 exists for 32-row blocks only)
+  const Cand want = {pref == 16 && t == 16 ? 0 : pref, pref == 8 && t == 32 ? 256 : 512, pref != 4};
   const Cand c16[4] = {{8, 512, true}, {4, 512, false}, {4, 1024, false}, {4, 1024, false}};
-  const Cand c32[4] = {{pref, pref == 8 ? 256 : 512, pref != 4}, {8, 256, true}, {8, 512, true}, {4, 512, false}};
-  const Cand* cand = t == 16 ? c16 : c32;
-  for (int k = 0; k < 4; k++) {
-    const int R = cand[k].R, NT = cand[k].NT;
+  const Cand c32[4] = {{8, 256, true}, {8, 512, true}, {4, 512, false}, {4, 512, false}};
+  const Cand* rule = t == 16 ? c16 : c32;
+  for (int k = pref ? -1 : 0; k < 4; k++) {
+    const Cand* cand = k < 0 ? &want : rule;
+    const int idx = k < 0 ? 0 : k;
+    const int R = cand[idx].R, NT = cand[idx].NT;
     if (R != 4 && R != 8 && R != 16) continue;
     const int m_max = NT / R;
     const int C = (M + m_max - 1) / m_max;
@@ -661,7 +664,7 @@ bool tdm_refined_shape(int M, int t, RefShape& sh) {
     sh.R = R; sh.NT = NT; sh.m = m; sh.C = C;
     sh.threads = ((m * R + 31) / 32) * 32;
     if (sh.threads < 96) sh.threads = 96;
-    sh.sm_coef = cand[k].sm;
+    sh.sm_coef = cand[idx].sm;
     sh.smem = refine_offsets(R, t, NT, sh.sm_coef).bytes;
     if (sh.smem > 227 * 1024) continue;
     return true;
@@ -709,7 +712,7 @@ RefItem tdm_refined_item(const tdm_plan_s* p, const float* F, int64_t ldF, doubl
 tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX, int64_t N,
                               cudaStream_t s) {
   RefShape sh;
-  if (!tdm_refined_shape(p->M, p->t, sh)) return TDM_ERR_NOT_IMPLEMENTED;
+  if (!tdm_refined_shape(p->M, p->t, p->tile_rhs, sh)) return TDM_ERR_NOT_IMPLEMENTED;
   const RefItem one = tdm_refined_item(p, F, ldF, X, ldX, N, 0);
   const int ntiles = (int)((N + sh.R - 1) / sh.R);
   return tdm_refined_launch(sh, p->t, nullptr, &one, ntiles, p->dev_err, s);

@@ -37,7 +37,8 @@ struct RefShape {
   size_t smem = 0;
 };
 
-bool tdm_refined_shape(int M, int t, RefShape& sh);
+// pref: requested right-hand sides per tile (0 = by the rule)
+bool tdm_refined_shape(int M, int t, int pref, RefShape& sh);
 // enqueue one launch over `nitems` items (items == nullptr: single series `one`)
 tdm_status tdm_refined_launch(const RefShape& sh, int t, const RefItem* items, const RefItem* one,
                               int nitems, int* err, cudaStream_t s);

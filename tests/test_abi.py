@@ -70,6 +70,9 @@ def test_bad_block_rows_rejected_before_any_cuda_call(lib):
     opt = TDMOptions(24, 0, 0, 0)
     assert lib.tdm_prepare(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), 100, ctypes.byref(opt),
                            None, ctypes.byref(h)) == 1
+    opt = TDMOptions(32, 0, 0, 5)            # tile_rhs must be 0, 4, 8 or 16
+    assert lib.tdm_prepare(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), 100, ctypes.byref(opt),
+                           None, ctypes.byref(h)) == 1
     opt = TDMOptions(32, -2, 0, 0)
     assert lib.tdm_prepare(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), 100, ctypes.byref(opt),
                            None, ctypes.byref(h)) == 1
