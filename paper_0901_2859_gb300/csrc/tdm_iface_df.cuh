@@ -38,7 +38,9 @@ struct IfaceOffsets {
   size_t ksR, ksL;   // pair [5][32] lane-range products: [i - 2^l + 1, i] and [i, i + 2^l - 1]
   size_t piR, piL;   // pair [MM+1] aR_0 .. aR_{j-1}; aL_j .. aL_{m-1}
   size_t wR, wL;     // pair [16] fold weights of the CTAs to the left / right
-  size_t xch;        // pair [2 parity][2 dir][R] this CTA's totals, read by the other CTAs
+  size_t xch;        // pair [2 parity][2 dir][R] this CTA's totals, read by the other CTAs (pairs)
+  size_t xin;        // float [2 parity][16 source CTA][R+1] totals pushed by the other CTAs (binary32)
+  size_t xbar;       // mbarrier [2 parity] completion of the pushed totals (binary32)
   size_t in;         // pair [2][R] in_R, in_L
   size_t tmp;        // double [96] set-up scratch
   size_t bytes;
@@ -61,7 +63,11 @@ __host__ __device__ constexpr IfaceOffsets iface_offsets(int R, int MM, bool pai
   o.piL = p; p += round16(8 * (size_t)(MM + 1));
   o.wR = p; p += 8 * 16;
   o.wL = p; p += 8 * 16;
-  o.xch = p; p += round16(8 * 4 * (size_t)R);
+  // pairs: the other CTAs read the totals remotely (xch); binary32: every CTA
+  // pushes its totals into the others' xin (see iface_push_send)
+  o.xch = p; p += pair ? round16(8 * 4 * (size_t)R) : 0;
+  o.xin = p; p += pair ? 0 : round16(4 * 2 * 16 * (size_t)(R + 1));
+  o.xbar = p; p += pair ? 0 : 16;
   o.in = p; p += round16(8 * 2 * (size_t)R);
   o.tmp = p; p += 8 * 96;
   o.bytes = p;
@@ -108,6 +114,8 @@ struct IfaceDF {
   __device__ float2* wR() const { return reinterpret_cast<float2*>(base + O.wR); }
   __device__ float2* wL() const { return reinterpret_cast<float2*>(base + O.wL); }
   __device__ float2* xch() const { return reinterpret_cast<float2*>(base + O.xch); }
+  __device__ float* xin() const { return reinterpret_cast<float*>(base + O.xin); }
+  __device__ uint64_t* xbar() const { return reinterpret_cast<uint64_t*>(base + O.xbar); }
   __device__ float2* in() const { return reinterpret_cast<float2*>(base + O.in); }
   __device__ double* tmp() const { return reinterpret_cast<double*>(base + O.tmp); }
 };
@@ -302,10 +310,60 @@ __device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM, PAIR>& f, int
       f.st_ll(m * RP + r, f2pair{0.f, 0.f});
     }
     __syncwarp();
-    if (lane == 0) {
-      f.xch()[(parity * 2 + 0) * R + r] = f2(f.ld_lr(m * RP + r));
-      f.xch()[(parity * 2 + 1) * R + r] = f2(f.ld_ll(r));
+    if constexpr (PAIR) {
+      if (lane == 0) {
+        f.xch()[(parity * 2 + 0) * R + r] = f2(f.ld_lr(m * RP + r));
+        f.xch()[(parity * 2 + 1) * R + r] = f2(f.ld_ll(r));
+      }
     }
+  }
+}
+
+// binary32: this CTA's totals of every column pushed into the other CTAs'
+// shared memory (after iface_df_scan, by the same warps): CTA cc receives
+// LR_m when it lies to the right, LL_0 when it lies to the left, at
+// xin[parity][c][r], and its barrier xbar[parity] counts the bytes.  No
+// memory fence is needed: the store carries its own completion.
+__device__ __forceinline__ void st_async_cluster_f32(float* local_dst, unsigned rank, float v, uint64_t* local_bar) {
+  const unsigned ldst = (unsigned)__cvta_generic_to_shared(local_dst);
+  const unsigned lbar = (unsigned)__cvta_generic_to_shared(local_bar);
+  unsigned rdst, rbar;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rdst) : "r"(ldst), "r"(rank));
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rbar) : "r"(lbar), "r"(rank));
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+               ::"r"(rdst), "r"(__float_as_uint(v)), "r"(rbar) : "memory");
+}
+template <int R, int MM>
+__device__ __forceinline__ void iface_push_send(const IfaceDF<R, MM, false>& f, int m, int C, unsigned c, int parity) {
+  constexpr int RP = IfaceDF<R, MM, false>::kRP;
+  const int lane = threadIdx.x & 31;
+  for (int r = threadIdx.x >> 5; r < R; r += blockDim.x >> 5) {
+    if (lane < C && lane != (int)c) {
+      const float v = lane > (int)c ? f.ld_lr(m * RP + r).h : f.ld_ll(r).h;
+      st_async_cluster_f32(f.xin() + (parity * 16 + (int)c) * (R + 1) + r, (unsigned)lane, v, f.xbar() + parity);
+    }
+  }
+}
+// bytes that arrive at xbar[parity] per tile
+template <int R>
+__host__ __device__ constexpr uint32_t iface_push_bytes(int C) { return (uint32_t)((C - 1) * R * 4); }
+
+// binary32 fold of the pushed totals (after xbar[parity] completed): one warp
+// per column, lanes 0-15 for the CTAs to the left, 16-31 for those to the
+// right, all reads local.
+template <int R, int MM>
+__device__ __forceinline__ void iface_push_fold(const IfaceDF<R, MM, false>& f, int C, unsigned c, int parity) {
+  const int lane = threadIdx.x & 31, cc = lane & 15;
+  const bool left = lane < 16;
+  const bool valid = left ? (cc < (int)c) : (cc > (int)c && cc < C);
+  const float w = valid ? (left ? f.wR()[cc].x : f.wL()[cc].x) : 0.f;
+  const float* src = f.xin() + (parity * 16 + cc) * (R + 1);
+  for (int r = threadIdx.x >> 5; r < R; r += blockDim.x >> 5) {
+    float v = valid ? w * src[r] : 0.f;
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) f.in()[r] = make_float2(v, 0.f);
+    if (lane == 16) f.in()[R + r] = make_float2(v, 0.f);
   }
 }
 

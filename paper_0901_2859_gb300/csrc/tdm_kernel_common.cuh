@@ -84,8 +84,9 @@ struct Smem {
 __host__ __device__ inline size_t fbuf_bytes(int m, int t, int R, int tsize, bool tma) {
   return tma ? (size_t)m * t * R * tsize : 0;
 }
+constexpr int kCPAD = 4;   // elements after each block's coefficient rows (bank offset between blocks)
 __host__ __device__ inline size_t coef_bytes(int m, int t, int tsize) {
-  return (size_t)m * t * kNCOEF * tsize;
+  return (size_t)m * (t * kNCOEF + kCPAD) * tsize;
 }
 __host__ __device__ inline size_t smem_bytes(int m, int t, int R, int tsize, bool tma) {
   // interface arrays as laid out by carve(), each rounded up to 16 bytes
@@ -96,6 +97,15 @@ __host__ __device__ inline size_t smem_bytes(int m, int t, int R, int tsize, boo
   return 128 + fbuf_bytes(m, t, R, tsize, tma) + coef_bytes(m, t, tsize) + d + f + tb;
 }
 
+// 2 coefficients starting at p (8-byte aligned for binary32) in one vector load
+__device__ __forceinline__ void ld2(const float* p, float& x, float& y) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  x = v.x; y = v.y;
+}
+__device__ __forceinline__ void ld2(const double* p, double& x, double& y) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  x = v.x; y = v.y;
+}
 // the 4 coefficients starting at p (16-byte aligned) in one or two vector loads
 __device__ __forceinline__ void ld4(const float* p, float& x, float& y, float& z, float& w) {
   const float4 v = *reinterpret_cast<const float4*>(p);
@@ -271,7 +281,8 @@ __device__ __forceinline__ void backward_y_plain(T (&v)[TT], const T* cf, int nr
 #pragma unroll
   for (int i = TT - 1; i >= 0; i--) {
     if (FULL || i < nrows) {
-      const T cc = cf[i * kNCOEF + kC], invd = cf[i * kNCOEF + kINVD];
+      T cc, invd;
+      ld2(cf + i * kNCOEF + kC, cc, invd);
       y = fma(-cc, y, v[i]) * invd;
       v[i] = y;
     }
@@ -283,7 +294,9 @@ __device__ __forceinline__ void correct_store(const T (&v)[TT], const T* cf, int
 #pragma unroll
   for (int i = 0; i < TT; i++) {
     if (FULL || i < nrows) {
-      const T x = fma(cf[i * kNCOEF + kPHIR], xR, fma(cf[i * kNCOEF + kPHIL], xL, v[i]));
+      T phl, phr;
+      ld2(cf + i * kNCOEF + kPHIL, phl, phr);
+      const T x = fma(phr, xR, fma(phl, xL, v[i]));
       if (col_ok) *p = x;
     }
     p += ld;

@@ -117,12 +117,21 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
       const int64_t row = cta_row0 + (k * 4) / kNCOEF;
       T x = T(0), y = T(0), z = T(0), w = T(0);
       if (row < n) ld4(coef + cta_row0 * kNCOEF + (int64_t)k * 4, x, y, z, w);
-      T* d = scf + (size_t)k * 4;
+      T* d = scf + (size_t)k * 4 + (size_t)((k * 4) / (TT * kNCOEF)) * kCPAD;
       d[0] = x; d[1] = y; d[2] = z; d[3] = w;
     }
   }
   if (TMA && tid == 0) tdm_mbar_init(&mbar, 1);
-  __syncthreads();
+  if constexpr (sizeof(T) == 4) {
+    if (tid == 0) {
+      tdm_mbar_init(f.xbar() + 0, 1);
+      tdm_mbar_init(f.xbar() + 1, 1);
+    }
+    // every CTA's exchange barriers exist before any CTA pushes to them
+    cluster_barrier();
+  } else {
+    __syncthreads();
+  }
 
   const int cluster_id = blockIdx.x / a.C;
   const int nclusters = gridDim.x / a.C;
@@ -136,11 +145,15 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
   if (TMA && tid == 0 && cluster_id < a.ntiles) issue(cluster_id);
 
   uint32_t phase = 0;
+  uint32_t xphase = 0;   // bit p: phase of xbar[p]
   bool abort = false;
   int parity = 0;
   for (int tile = cluster_id; tile < a.ntiles; tile += nclusters) {
     const int64_t col = (int64_t)tile * R + r;
     const bool col_ok = col < a.N;
+    if constexpr (sizeof(T) == 4) {
+      if (tid == 0) tdm_mbar_expect_tx(f.xbar() + parity, iface_push_bytes<R>(a.C));
+    }
     T v[TT];
     if constexpr (TMA) {
       if (!abort && !tdm_mbar_wait_cta(&mbar, phase, a.err, &wait_ok)) abort = true;
@@ -160,7 +173,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
       for (int i = 0; i < TT; i++) v[i] = (i < nrows && col_ok) ? Fp[(int64_t)i * a.ldF] : T(0);
     }
     // A2 + A3 forward: one pass over the rows
-    const T* cfb = scf + (size_t)bl * TT * kNCOEF;
+    const T* cfb = scf + (size_t)bl * (TT * kNCOEF + kCPAD);
     T bR = T(0), bL = T(0);
     if (nrows == TT) forward_pass<T, TT, true>(v, cfb, nrows, bR, bL);
     else forward_pass<T, TT, false>(v, cfb, nrows, bR, bL);
@@ -183,11 +196,13 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
       }
       __syncthreads();
       iface_df_scan<R, MM, false>(f, a.m, parity);
-      cluster_arrive();   // the back substitution overlaps the exchange of the CTA totals
+      iface_push_send<R, MM>(f, a.m, a.C, c, parity);
+      // the back substitution overlaps the exchange of the CTA totals
       if (nrows == TT) backward_y_plain<T, TT, true>(v, cfb, nrows);
       else backward_y_plain<T, TT, false>(v, cfb, nrows);
-      cluster_wait();
-      iface_df_fold<R, MM, false>(f, a.C, c, parity);
+      if (!abort && !tdm_mbar_wait(f.xbar() + parity, (xphase >> parity) & 1u, a.err)) abort = true;
+      xphase ^= 1u << parity;
+      iface_push_fold<R, MM>(f, a.C, c, parity);
       __syncthreads();
       if (blk_ok) {
         if (b >= 1) xL = iface_df_sep<R, MM, false>(f, bl, r);
