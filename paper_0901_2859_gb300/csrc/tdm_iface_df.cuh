@@ -207,8 +207,8 @@ __device__ __forceinline__ void iface_df_setup(const IfaceDF<R, MM, PAIR>& f, co
   double* AL = f.tmp() + 32;
   double* TR = f.tmp() + 64;   // [16] CTA totals
   double* TL = f.tmp() + 80;
-  for (int u = tid; u < 64 + 2 + 2 * C; u += nt) {
-    if (u < 64) {   // one lane of one direction: multipliers, in-lane products, lane product
+  for (int u = tid; u < 64; u += nt) {
+    {               // one lane of one direction: multipliers, in-lane products, lane product
       const int lane = u & 31;
       double p = 1.0;
       if (lane < nl) {
@@ -220,20 +220,24 @@ __device__ __forceinline__ void iface_df_setup(const IfaceDF<R, MM, PAIR>& f, co
         }
       }
       (u < 32 ? AR : AL)[lane] = p;
-    } else if (u == 64) {   // prefix products from the left
-      double p = 1.0;
-      f.piR()[0] = df_of(1.0);
-      for (int j = 1; j <= m; j++) { p *= gR(b0 + j - 1); f.piR()[j] = df_of(p); }
-    } else if (u == 65) {   // from the right
-      double p = 1.0;
-      f.piL()[m] = df_of(1.0);
-      for (int j = m - 1; j >= 0; j--) { p *= gL(b0 + j + 1); f.piL()[j] = df_of(p); }
-    } else {                // the totals of every CTA of the cluster
-      const int k = u - 66, cc = k % C;
-      double p = 1.0;
-      if (k < C) for (int j = 0; j < m; j++) p *= gR(cc * m + j);
-      else for (int j = 0; j < m; j++) p *= gL(cc * m + j + 1);
-      (k < C ? TR : TL)[cc] = p;
+    }
+  }
+  // prefix products from the left and from the right, and the totals of every
+  // CTA of the cluster (one warp per CTA and direction); each warp loads its
+  // factors together and multiplies in logarithmic depth
+  const int warp = tid >> 5, nwarps = nt >> 5;
+  if (warp == 0) {
+    if (tid == 0) f.piR()[0] = df_of(1.0);
+    warp_scan_products(m, false, [&](int j) { return gR(b0 + j); }, [&](int j, double p) { f.piR()[j + 1] = df_of(p); });
+  } else if (warp == 1) {
+    if (tid == 32) f.piL()[m] = df_of(1.0);
+    warp_scan_products(m, true, [&](int j) { return gL(b0 + j + 1); }, [&](int j, double p) { f.piL()[j] = df_of(p); });
+  } else {
+    for (int k = warp - 2; k < 2 * C; k += nwarps - 2) {
+      const int cc = k % C;
+      const double p = k < C ? warp_products(m, [&](int j) { return gR(cc * m + j); })
+                             : warp_products(m, [&](int j) { return gL(cc * m + j + 1); });
+      if ((tid & 31) == 0) (k < C ? TR : TL)[cc] = p;
     }
   }
   __syncthreads();

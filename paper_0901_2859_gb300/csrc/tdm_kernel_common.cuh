@@ -150,6 +150,51 @@ __device__ __forceinline__ unsigned smem_align_pad(const void* smem_base) {
 
 // Ratios, prefix products within this CTA, and the per-CTA products of every
 // CTA of the cluster (used to fold the incoming partials).
+// Products of the separator ratios, by one warp in logarithmic depth (the
+// factors are loaded together rather than one dependent load at a time):
+//   warp_scan_products: out(j) = f(0) ... f(j) for j < m (inclusive prefix;
+//     with `suffix`, out(j) = f(j) ... f(m-1));
+//   warp_products: f(0) ... f(m-1), returned in every lane.
+// Each lane takes up to 8 consecutive factors (m <= 256).
+template <typename Get, typename Put>
+__device__ __forceinline__ void warp_scan_products(int m, bool suffix, Get f, Put out) {
+  const int lane = threadIdx.x & 31;
+  const int K = (m + 31) / 32;
+  double v[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const int pos = lane * K + k;
+    v[k] = (k < K && pos < m) ? f(suffix ? m - 1 - pos : pos) : 1.0;
+  }
+  double p = 1.0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) p *= v[k];
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double o = __shfl_up_sync(0xffffffffu, p, d);
+    if (lane >= d) p *= o;
+  }
+  double q = __shfl_up_sync(0xffffffffu, p, 1);
+  if (lane == 0) q = 1.0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const int pos = lane * K + k;
+    if (k < K && pos < m) {
+      q *= v[k];
+      out(suffix ? m - 1 - pos : pos, q);
+    }
+  }
+}
+template <typename Get>
+__device__ __forceinline__ double warp_products(int m, Get f) {
+  const int lane = threadIdx.x & 31;
+  double p = 1.0;
+  for (int j = lane; j < m; j += 32) p *= f(j);
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) p *= __shfl_xor_sync(0xffffffffu, p, o);
+  return p;
+}
+
 __device__ inline void setup_ratios(const SolveArgs& a, const Smem& s, unsigned c) {
   const int m = a.m, M = a.M, b0 = (int)c * m;
   auto rR = [&](int q) -> double { return (q >= 0 && q <= M + 1) ? a.rR[q] : 0.0; };
@@ -159,23 +204,22 @@ __device__ inline void setup_ratios(const SolveArgs& a, const Smem& s, unsigned 
     s.rRloc[j] = (j >= 1) ? rR(b0 + j - 1) : 0.0;
     s.rLloc[j] = (j < m) ? rL(b0 + j + 1) : 0.0;
   }
-  if (tid == 0) {
-    double p = 1.0;
-    s.piR[0] = 1.0;
-    s.piR32[0] = 1.0f;
-    for (int j = 1; j <= m; j++) { p *= rR(b0 + j - 1); s.piR[j] = p; s.piR32[j] = (float)p; }
-  } else if (tid == 32) {
-    double p = 1.0;
-    s.piL[m] = 1.0;
-    s.piL32[m] = 1.0f;
-    for (int j = m - 1; j >= 0; j--) { p *= rL(b0 + j + 1); s.piL[j] = p; s.piL32[j] = (float)p; }
-  } else if (tid >= 64 && tid < 64 + a.C) {
-    const int cc = tid - 64, bb = cc * m;
-    double pr = 1.0, pl = 1.0;
-    for (int j = 1; j <= m; j++) pr *= rR(bb + j - 1);
-    for (int j = m - 1; j >= 0; j--) pl *= rL(bb + j + 1);
-    s.piRtot[cc] = pr;
-    s.piLtot[cc] = pl;
+  const int warp = tid >> 5, nwarps = blockDim.x >> 5;
+  if (warp == 0) {          // piR_j = rR_{b0} ... rR_{b0+j-1}
+    if (tid == 0) { s.piR[0] = 1.0; s.piR32[0] = 1.0f; }
+    warp_scan_products(m, false, [&](int j) { return rR(b0 + j); },
+                       [&](int j, double p) { s.piR[j + 1] = p; s.piR32[j + 1] = (float)p; });
+  } else if (warp == 1) {   // piL_j = rL_{b0+j+1} ... rL_{b0+m}
+    if (tid == 32) { s.piL[m] = 1.0; s.piL32[m] = 1.0f; }
+    warp_scan_products(m, true, [&](int j) { return rL(b0 + j + 1); },
+                       [&](int j, double p) { s.piL[j] = p; s.piL32[j] = (float)p; });
+  } else {                  // every CTA's totals, one warp per CTA and direction
+    for (int k = warp - 2; k < 2 * a.C; k += nwarps - 2) {
+      const int cc = k % a.C, bb = cc * m;
+      const double p = k < a.C ? warp_products(m, [&](int j) { return rR(bb + j); })
+                               : warp_products(m, [&](int j) { return rL(bb + j + 1); });
+      if ((tid & 31) == 0) (k < a.C ? s.piRtot : s.piLtot)[cc] = p;
+    }
   }
 }
 
