@@ -1,4 +1,5 @@
-"""CPU oracle for the variable-separation (Fourier) Poisson solver of Section 4a.
+"""CPU oracle for the Poisson solvers of Section 4: variable separation (Fourier,
+Section 4a) and alternating directions (Peaceman-Rachford, Section 4b).
 
 TEST INFRASTRUCTURE ONLY: the tests and ``bench.py``'s CPU legs use this
 module; the product path never imports it.  It shares no code with the
@@ -25,9 +26,12 @@ Steps (Section 4a, eqs. fft_phi, SLAU_FFT):
      with u~_0 = u~_{N1} = 0, solved by the sweep;
   3. the synthesis u[i,j] = sum_l u~_i(l) sin(pi l j / N2).
 
-Pins (``tests/test_oracle_pins.py``): the model problem of eq. poisson_test,
-whose discrete solution is one eigenmode in closed form; the discrete equation
-itself (the residual of the oracle's u); the orthogonality of the sine basis.
+Pins (``tests/test_poisson_oracle.py``): the model problem of eq. poisson_test,
+whose discrete solution is one eigenmode in closed form; brute force on tiny
+meshes (the dense five-point system); scipy's DST-I; the discrete equation
+itself (the residual of the oracle's u); for the alternating directions, the
+parameter count of eq. ocenka1 worked by hand, the fixed point, and the
+accuracy eps reached against the pinned Fourier solution.
 """
 from __future__ import annotations
 
@@ -95,3 +99,59 @@ def model_problem(N1: int, N2: int):
     f = 8.0 * np.pi ** 2 * np.outer(sx, sy)
     lam = 4.0 / h1 ** 2 * np.sin(np.pi * h1) ** 2 + 4.0 / h2 ** 2 * np.sin(np.pi * h2) ** 2
     return f, f / lam, h1, h2
+
+
+# --------------------------------------------------------------------------
+# Alternating directions (Section 4b): the Peaceman-Rachford iteration
+# (eqs. adi_iter, adi_iter2) on the square mesh N1 = N2 = N, h = 1/N.
+#
+# Readings (the paper leaves them open):
+#  * sign: the iteration relaxes du/dt = Lambda u + f, whose steady state is
+#    the discrete problem Lambda u = -f of eq. poisson_difference;
+#  * parameters: omega_k = 1/tau_k (tau^(1) = tau^(2)), a geometric sequence
+#    over the spectrum [delta, Delta] of -Lambda_alpha, delta = (4/h^2)
+#    sin^2(pi h / 2), Delta = (4/h^2) cos^2(pi h / 2), endpoints included;
+#  * their number n_0(eps) = ceil(0.2 ln(4N/pi) ln(4/eps)) (eq. ocenka1),
+#    applied once each from u = 0.
+# --------------------------------------------------------------------------
+
+def adi_parameters(N: int, eps: float) -> np.ndarray:
+    """omega_1..omega_{n0} for the N x N mesh and accuracy eps."""
+    h = 1.0 / N
+    lo = 4.0 / h ** 2 * np.sin(np.pi * h / 2.0) ** 2
+    hi = 4.0 / h ** 2 * np.cos(np.pi * h / 2.0) ** 2
+    n0 = int(np.ceil(0.2 * np.log(4.0 * N / np.pi) * np.log(4.0 / eps)))
+    k = np.arange(n0, dtype=np.float64)
+    return lo * (hi / lo) ** (k / max(n0 - 1, 1))
+
+
+def _second_difference(u, axis: int, h: float) -> np.ndarray:
+    pad = [(0, 0)] * u.ndim
+    pad[axis] = (1, 1)
+    U = np.pad(u, pad)
+    sl = lambda a, b: tuple(slice(a, b) if d == axis else slice(None) for d in range(u.ndim))
+    return (U[sl(2, None)] - 2.0 * U[sl(1, -1)] + U[sl(None, -2)]) / h ** 2
+
+
+def peaceman_rachford(f, N: int, omegas) -> np.ndarray:
+    """u after one pass over `omegas`, from u = 0; f of shape (N-1, N-1) or (N-1, N-1, S).
+    Each step solves (omega I - Lambda_1) u' = (omega I + Lambda_2) u + f along i, then
+    (omega I - Lambda_2) u'' = (omega I + Lambda_1) u' + f along j, scaled by h^2 into
+    tridiag(-1, 2 + omega h^2, -1) systems solved by the sweep."""
+    f = np.asarray(f, dtype=np.float64)
+    series = f.ndim == 3
+    if not series:
+        f = f[:, :, None]
+    n, _, S = f.shape
+    h = 1.0 / N
+    u = np.zeros_like(f)
+    a = -np.ones(n - 1)
+    for om in omegas:
+        b = np.full(n, 2.0 + om * h * h)
+        rhs = h * h * (om * u + _second_difference(u, 1, h) + f)         # along i; columns (j, s)
+        uh = thomas_f64(a, b, rhs.reshape(n, n * S)).reshape(n, n, S)
+        rhs = h * h * (om * uh + _second_difference(uh, 0, h) + f)       # along j; columns (i, s)
+        rt = np.ascontiguousarray(rhs.transpose(1, 0, 2)).reshape(n, n * S)
+        u = thomas_f64(a, b, rt).reshape(n, n, S).transpose(1, 0, 2)
+    u = np.ascontiguousarray(u)
+    return u if series else u[:, :, 0]

@@ -62,3 +62,49 @@ def test_planted_mistakes_are_caught(monkeypatch):
     good_s = op.sine_matrix
     monkeypatch.setattr(op, "sine_matrix", lambda N2: good_s(N2 + 1)[:N2 - 1, :N2 - 1])
     assert np.max(np.abs(op.fourier_poisson(f, h1, h2) - ref)) > 1e-6 * np.max(np.abs(ref))
+
+
+# ---- alternating directions (Section 4b) ------------------------------------
+
+@pytest.mark.parametrize("N,eps,n0", [(512, 1e-5, 17), (1024, 1e-5, 19), (64, 1e-3, 8)])
+def test_adi_parameter_count_eq_ocenka1(N, eps, n0):
+    # n0 = ceil(0.2 ln(4N/pi) ln(4/eps)), worked by hand: N=512: 0.2*6.480*12.899 = 16.72;
+    # N=1024: 0.2*7.173*12.899 = 18.51; N=64, eps=1e-3: 0.2*4.401*8.294 = 7.30
+    w = op.adi_parameters(N, eps)
+    assert len(w) == n0
+    h = 1.0 / N
+    assert np.isclose(w[0], 4 / h ** 2 * np.sin(np.pi * h / 2) ** 2)
+    assert np.isclose(w[-1], 4 / h ** 2 * np.cos(np.pi * h / 2) ** 2)
+    assert np.allclose(w[1:] / w[:-1], w[1] / w[0])   # geometric
+
+
+def test_adi_fixed_point_is_the_discrete_solution():
+    # one Peaceman-Rachford step from the exact discrete solution returns it
+    N = 24
+    f, u, h1, h2 = op.model_problem(N, N)
+    rng = np.random.default_rng(2)
+    fr = rng.standard_normal((N - 1, N - 1))
+    ur = op.fourier_poisson(fr, 1.0 / N, 1.0 / N)
+    h = 1.0 / N
+    for om in (3.0, 500.0):
+        b = np.full(N - 1, 2.0 + om * h * h)
+        a = -np.ones(N - 2)
+        import oracle
+        rhs = h * h * (om * ur + op._second_difference(ur, 1, h) + fr)
+        uh = oracle.thomas_f64(a, b, rhs)
+        assert np.max(np.abs(uh - ur)) <= 1e-11 * np.max(np.abs(ur))
+
+
+@pytest.mark.parametrize("N", [32, 128])
+def test_adi_reaches_eps_against_the_fourier_solution(N):
+    eps = 1e-5
+    f, u, _, _ = op.model_problem(N, N)
+    got = op.peaceman_rachford(f, N, op.adi_parameters(N, eps))
+    assert np.max(np.abs(got - u)) <= eps * np.max(np.abs(u))
+    fr = np.random.default_rng(N).standard_normal((N - 1, N - 1, 2))
+    ref = op.fourier_poisson(fr, 1.0 / N, 1.0 / N)
+    got = op.peaceman_rachford(fr, N, op.adi_parameters(N, eps))
+    assert np.max(np.abs(got - ref)) <= eps * np.max(np.abs(ref))
+    # a planted mistake (omega scaled by h^2 twice) does not converge
+    bad = op.peaceman_rachford(fr, N, op.adi_parameters(N, eps) / N ** 2)
+    assert np.max(np.abs(bad - ref)) > 100 * eps * np.max(np.abs(ref))
