@@ -396,6 +396,55 @@ def run_poisson(args):
         print(json.dumps(line), flush=True)
 
 
+def run_adi(args):
+    """Alternating directions (Section 4b) on the paper's 1024 x 1024 mesh: a
+    series of 100 model problems iterated together to eps = 1e-5 (binary64
+    state, binary32 right-hand sides solved to binary64 results); the binary32
+    variant is timed beside it."""
+    import numpy as np
+    import torch
+    from paper_0901_2859_gb300.adi import PeacemanRachford
+    from paper_0901_2859_gb300.poisson import FourierPoisson
+
+    dev = torch.device("cuda", DIST["local"])
+    torch.cuda.set_device(dev)
+    N, nprob, eps = 1024, 100, 1e-5
+    t0 = time.perf_counter()
+    pr = PeacemanRachford(N, eps, precision="fp32_refined", device=dev)
+    torch.cuda.synchronize()
+    prepare_s = time.perf_counter() - t0
+    scale = torch.linspace(1.0, 2.0, nprob, dtype=torch.float64, device=dev)
+    f = FourierPoisson.model_rhs(N, N, device=dev)[:, :, None] * scale
+    steps = max(1, min(args.steps, 10))
+    ms = _events_time(lambda: pr.solve(f), steps, max(3, args.warmup), torch)
+    h = 1.0 / N
+    lam = 8.0 / h ** 2 * np.sin(np.pi * h) ** 2
+    u = pr.solve(f).double()
+    err = float((u - f / lam).abs().max() / (f / lam).abs().max())
+    iters = len(pr.omegas)
+    pr.close()
+    pr32 = PeacemanRachford(N, eps, precision="fp32", device=dev)
+    ms32 = _events_time(lambda: pr32.solve(f), steps, max(3, args.warmup), torch)
+    u32 = pr32.solve(f).double()
+    err32 = float((u32 - f / lam).abs().max() / (f / lam).abs().max())
+    pr32.close()
+    line = {
+        "metric": "Poisson problems solved/s (alternating directions to eps = 1e-5, series of 100)",
+        "value": nprob / (ms * 1e-3), "unit": "problems/s", "n_gpus": DIST["world"], "steps": steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "adi: eq. poisson_test on a 1024 x 1024 mesh, 100 right-hand sides, Peaceman-Rachford "
+                               "with n0(eps) geometric parameters, refined dichotomy solves (binary64 results)",
+                   "mesh": [N, N], "problems": nprob, "iterations": iters, "eps": eps},
+        "rel_err_vs_exact_discrete": err,
+        "binary32_path": {"ms": ms32, "problems_per_s": nprob / (ms32 * 1e-3), "rel_err_vs_exact_discrete": err32},
+        "prepare_s_all_parameters": prepare_s,
+        "paper_context": "about 30 problems/s on 1024 x 1024 (MBC-100k, best processor count; Table 2)",
+    }
+    if DIST["rank"] == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The oracle (the plain CPU implementation), timed on the host cores on a bounded sample."""
     N_RHS = args.rhs
@@ -440,9 +489,9 @@ def main():
     ap.add_argument("--cpu-cols", type=int, default=8192, help="columns of the CPU baseline sample")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline: seconds of repeated passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "poisson2d"],
+    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "poisson2d", "adi"],
                     help="precision: the benchmark line; batching: 512 matrices of uneven size in one launch; "
-                         "poisson2d: the Fourier method on a 1024 x 1024 mesh, 100 problems")
+                         "poisson2d: the Fourier method on a 1024 x 1024 mesh, 100 problems; adi: alternating directions")
     ap.add_argument("--rhs", type=int, default=N_RHS,
                     help="right-hand sides of the series (the benchmark is 8192; smaller values are for profiling)")
     args = ap.parse_args()
@@ -450,6 +499,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "adi":
+        run_adi(args)
     elif args.workload == "poisson2d":
         run_poisson(args)
     elif args.workload == "batching":
