@@ -22,6 +22,8 @@ numpy part (this file):
   z_vectors             Z^R_k, Z^L_k from eq. z_vector (for the Theorem 4 bound)
   explicit_inverse      the explicit inverse of Section 3.6 (eqs. x1-x3),
                         symmetric case
+  thomas_general        the sweep for a general (nonsymmetric) tridiagonal matrix
+  symmetrizer           the diagonal similarity that symmetrizes it (Section 3.5)
 Parity is pinned for every function here by ``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
@@ -368,3 +370,33 @@ def explicit_inverse(a, b):
     i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     # i <= j: y_i z_j;  i >= j: z_i y_j  -- both are y_min(i,j) * z_max(i,j)
     return y[np.minimum(i, j)] * z[np.maximum(i, j)]
+
+
+def thomas_general(sub, diag, sup, F):
+    """Textbook sweep in binary64 for a general tridiagonal matrix
+    (A[i][i] = diag[i], A[i+1][i] = sub[i], A[i][i+1] = sup[i]), every column
+    of F (shape (n,) or (n, N)); pure numpy, one row at a time."""
+    sub, diag, sup = _f64(sub), _f64(diag), _f64(sup)
+    F, squeeze = _as2d(F)
+    n = diag.shape[0]
+    X = np.array(F, dtype=np.float64, copy=True)
+    d = np.empty(n)
+    d[0] = diag[0]
+    for i in range(1, n):           # forward elimination
+        l = sub[i - 1] / d[i - 1]
+        d[i] = diag[i] - l * sup[i - 1]
+        X[i] -= l * X[i - 1]
+    X[n - 1] /= d[n - 1]
+    for i in range(n - 2, -1, -1):  # back substitution
+        X[i] = (X[i] - sup[i] * X[i + 1]) / d[i]
+    return X[:, 0] if squeeze else X
+
+
+def symmetrizer(sub, sup):
+    """t of the diagonal similarity of Section 3.5: with T = diag(t), T^{-1} A T
+    is symmetric when sub[k] * sup[k] > 0; t_0 = 1, t_{k+1} = t_k sqrt(sub[k] / sup[k])."""
+    sub, sup = _f64(sub), _f64(sup)
+    t = np.ones(sub.shape[0] + 1)
+    for k in range(sub.shape[0]):
+        t[k + 1] = t[k] * np.sqrt(sub[k] / sup[k])
+    return t

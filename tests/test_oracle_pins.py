@@ -271,3 +271,53 @@ def test_planted_mistakes_are_caught(oracle):
     assert _rel(oracle.thomas_f64(a2, np.roll(b2, 1), F2), ref) > 1e-3
     # right-hand side rows transposed
     assert _rel(oracle.thomas_f64(a2, b2, F2[::-1]), ref) > 1e-3
+
+
+# ---- nonsymmetric matrices (Section 3.5) ---------------------------------------
+
+def _general(n, seed, eps=0.3):
+    rng = np.random.default_rng(seed)
+    sub = -1.0 - eps * rng.random(n - 1)
+    sup = -1.0 + eps * rng.random(n - 1)
+    diag = 2.5 + rng.random(n)
+    return sub, diag, sup
+
+
+def _dense_general(sub, diag, sup):
+    return np.diag(diag) + np.diag(sub, -1) + np.diag(sup, 1)
+
+
+@pytest.mark.parametrize("n", [2, 7, 40])
+def test_thomas_general_matches_dense_solve(oracle, n):
+    sub, diag, sup = _general(n, n)
+    F = np.random.default_rng(1).standard_normal((n, 3))
+    ref = np.linalg.solve(_dense_general(sub, diag, sup), F)
+    assert np.max(np.abs(oracle.thomas_general(sub, diag, sup, F) - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_thomas_general_matches_scipy_banded(oracle):
+    linalg = pytest.importorskip("scipy.linalg")
+    n = 300
+    sub, diag, sup = _general(n, 9)
+    F = np.random.default_rng(2).standard_normal((n, 4))
+    ab = np.zeros((3, n))
+    ab[0, 1:], ab[1], ab[2, :-1] = sup, diag, sub
+    ref = linalg.solve_banded((1, 1), ab, F)
+    assert np.max(np.abs(oracle.thomas_general(sub, diag, sup, F) - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # the symmetric special case is the symmetric sweep
+    a = -np.ones(n - 1)
+    assert np.allclose(oracle.thomas_general(a, diag, a, F), oracle.thomas_f64(a, diag, F), rtol=0, atol=1e-14)
+
+
+def test_symmetrizer_section_3_5(oracle):
+    n = 25
+    sub, diag, sup = _general(n, 4, eps=0.6)
+    t = oracle.symmetrizer(sub, sup)
+    A = _dense_general(sub, diag, sup)
+    S = np.diag(1.0 / t) @ A @ np.diag(t)
+    assert np.max(np.abs(S - S.T)) <= 1e-14 * np.max(np.abs(S))
+    assert np.allclose(np.diag(S), diag)
+    # a planted mistake (the inverse ratio) breaks the symmetry
+    t_bad = 1.0 / t
+    S_bad = np.diag(1.0 / t_bad) @ A @ np.diag(t_bad)
+    assert np.max(np.abs(S_bad - S_bad.T)) > 1e-3
