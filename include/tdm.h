@@ -105,6 +105,7 @@ typedef struct {
                               1 = a TMA transfer timed out, 2 = refinement cap reached
                               before the convergence test passed) */
   int32_t tile_rhs;        /* the plan's tile_rhs option (0 = automatic) */
+  int32_t general;         /* 1 for a plan of tdm_prepare_general (a nonsymmetric matrix) */
 } tdm_info;
 
 /* tdm_prepare -- Algorithm 3/4, step 1 (Sections 3.3-3.4; eqs. green_v, z_vector).
@@ -121,6 +122,24 @@ typedef struct {
  * With refine_steps = 0 the call also runs one calibration solve (see tdm_options). */
 tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
                        const tdm_options* opt, void* stream, tdm_handle* out);
+
+/* tdm_prepare_general -- a nonsymmetric tridiagonal A, symmetrized by the
+ * diagonal similarity of Section 3.5: with T = diag(t), t_{k+1} = t_k
+ * (sub_k / sup_k)^(1/2), T^-1 A T is symmetric, and the plan of that matrix
+ * is prepared with every factor of T folded into its coefficients, so that
+ * the solves return x = A^-1 F.
+ *   sub    device, n-1 binary64 entries A[k+1][k]
+ *   diag   device, n binary64 entries A[k][k]
+ *   sup    device, n-1 binary64 entries A[k][k+1]
+ *   n, opt, stream, out as for tdm_prepare (tile_rhs and refine_steps are unused).
+ * Requires sub_k * sup_k > 0 for every k (the similarity exists); the factors
+ * of T within one block must stay finite in binary32 for TDM_FP32 solves.
+ * Errors: TDM_ERR_INVALID_ARG also when some sub_k * sup_k <= 0; the others as
+ * for tdm_prepare.  A general plan serves TDM_FP64 and TDM_FP32 solves,
+ * batched or not; TDM_FP32_REFINED solves and tdm_solve_backward return
+ * TDM_ERR_NOT_IMPLEMENTED for it. */
+tdm_status tdm_prepare_general(const double* sub, const double* diag, const double* sup, int64_t n,
+                               const tdm_options* opt, void* stream, tdm_handle* out);
 
 /* tdm_solve -- Algorithm 3/4, step 2 for every column (Theorem 2, Lemma 1).
  *   F   device, [n][ldF], dtype per `prec` (binary64 for TDM_FP64, else binary32)

@@ -16,7 +16,7 @@ STATUS_NAMES = {
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_refined": 2}
 
 # every symbol include/tdm.h declares
-EXPORTS = ("tdm_prepare", "tdm_solve", "tdm_solve_batched", "tdm_solve_batched_noalloc",
+EXPORTS = ("tdm_prepare", "tdm_prepare_general", "tdm_solve", "tdm_solve_batched", "tdm_solve_batched_noalloc",
            "tdm_solve_backward", "tdm_get_info", "tdm_destroy", "tdm_status_string")
 NOALLOC_MAX_TILES = 4096   # TDM_NOALLOC_MAX_TILES
 
@@ -30,7 +30,7 @@ class TDMInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("block_rows", ctypes.c_int32), ("num_blocks", ctypes.c_int32),
                 ("dominant", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("max_abs_z", ctypes.c_double), ("min_abs_pivot", ctypes.c_double),
-                ("device_error", ctypes.c_int32), ("tile_rhs", ctypes.c_int32)]
+                ("device_error", ctypes.c_int32), ("tile_rhs", ctypes.c_int32), ("general", ctypes.c_int32)]
 
 
 class TDMError(RuntimeError):
@@ -61,6 +61,7 @@ def load(build_if_missing: bool = True):
         lib = ctypes.CDLL(path)
         vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         lib.tdm_prepare.argtypes = [vp, vp, i64, ctypes.POINTER(TDMOptions), vp, ctypes.POINTER(vp)]
+        lib.tdm_prepare_general.argtypes = [vp, vp, vp, i64, ctypes.POINTER(TDMOptions), vp, ctypes.POINTER(vp)]
         lib.tdm_solve.argtypes = [vp, vp, i64, vp, i64, i64, i32, vp]
         lib.tdm_solve_batched.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                                           ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i64), i32, vp]

@@ -40,7 +40,9 @@ class Plan:
     """A prepared matrix (Algorithm 3/4 step 1).  Owns device memory until closed."""
 
     def __init__(self, a: torch.Tensor, b: torch.Tensor, block_rows: int = 0, refine_steps: int = 0,
-                 tile_rhs: int = 0):
+                 tile_rhs: int = 0, sup: torch.Tensor | None = None):
+        """A = tridiag(a, b, a); with `sup`, the nonsymmetric A with sub-diagonal a
+        (A[k+1][k]) and super-diagonal sup (A[k][k+1]) (Section 3.5)."""
         lib = _lib.load()
         if not (isinstance(b, torch.Tensor) and b.is_cuda):
             raise TypeError("a and b must be CUDA tensors (float64)")
@@ -49,16 +51,28 @@ class Plan:
         b = b.to(dtype=torch.float64).contiguous()
         if a.numel() != max(n - 1, 0):
             raise ValueError(f"a must have n-1 = {n - 1} entries, got {a.numel()}")
+        if sup is not None:
+            sup = sup.to(device=b.device, dtype=torch.float64).contiguous()
+            if sup.numel() != max(n - 1, 0):
+                raise ValueError(f"sup must have n-1 = {n - 1} entries, got {sup.numel()}")
         self.device = b.device
         self.n = n
+        self.general = sup is not None
         opts = TDMOptions(block_rows, refine_steps, 0, tile_rhs)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            st = lib.tdm_prepare(ctypes.c_void_p(a.data_ptr() if n > 1 else 0), ctypes.c_void_p(b.data_ptr()),
-                                 n, ctypes.byref(opts), _stream_ptr(self.device), ctypes.byref(h))
-        check(st, "tdm_prepare")
+            if self.general:
+                st = lib.tdm_prepare_general(ctypes.c_void_p(a.data_ptr() if n > 1 else 0),
+                                             ctypes.c_void_p(b.data_ptr()),
+                                             ctypes.c_void_p(sup.data_ptr() if n > 1 else 0), n,
+                                             ctypes.byref(opts), _stream_ptr(self.device), ctypes.byref(h))
+            else:
+                st = lib.tdm_prepare(ctypes.c_void_p(a.data_ptr() if n > 1 else 0), ctypes.c_void_p(b.data_ptr()),
+                                     n, ctypes.byref(opts), _stream_ptr(self.device), ctypes.byref(h))
+        check(st, "tdm_prepare_general" if self.general else "tdm_prepare")
         self._h = h
         self.a, self.b = a, b   # kept for autograd and the residual-free properties
+        self.sup = sup
 
     @property
     def handle(self):
@@ -127,6 +141,16 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def prepare_general(sub, diag, sup, block_rows: int = 0, device=None) -> Plan:
+    """Prepare a nonsymmetric tridiagonal A (A[k+1][k] = sub[k], A[k][k] = diag[k],
+    A[k][k+1] = sup[k]) with every sub[k] * sup[k] > 0: symmetrized by the
+    diagonal similarity of Section 3.5.  The plan serves "fp64" and "fp32" solves."""
+    dev = torch.device(device) if device is not None else (
+        diag.device if isinstance(diag, torch.Tensor) and diag.is_cuda else torch.device("cuda", torch.cuda.current_device()))
+    as_dev = lambda x: torch.as_tensor(x, dtype=torch.float64).to(dev)
+    return Plan(as_dev(sub), as_dev(diag), block_rows=block_rows, sup=as_dev(sup))
 
 
 def prepare(a, b, block_rows: int = 0, refine_steps: int = 0, device=None, tile_rhs: int = 0) -> Plan:

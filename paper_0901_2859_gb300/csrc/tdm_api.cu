@@ -24,6 +24,8 @@ tdm_status validate_solve(const tdm_plan_s* h, const void* F, int64_t ldF, const
                           int64_t ldX, int64_t N, tdm_precision prec) {
   if (!h) return TDM_ERR_INVALID_ARG;
   if (prec != TDM_FP64 && prec != TDM_FP32 && prec != TDM_FP32_REFINED) return TDM_ERR_INVALID_ARG;
+  // the refined residual is formed for a symmetric matrix (its edge fluxes are shared by both rows)
+  if (h->general && prec == TDM_FP32_REFINED) return TDM_ERR_NOT_IMPLEMENTED;
   if (N < 0 || N > (int64_t(1) << 40)) return TDM_ERR_INVALID_ARG;
   if (N == 0) return TDM_OK;
   if (!F || !X || ldF < N || ldX < N) return TDM_ERR_INVALID_ARG;
@@ -165,6 +167,7 @@ extern "C" tdm_status tdm_solve_backward(tdm_handle h, const void* W, const void
   if (!h) return TDM_ERR_INVALID_ARG;
   if (prec == TDM_FP32_REFINED) return TDM_ERR_NOT_IMPLEMENTED;
   if (prec != TDM_FP64 && prec != TDM_FP32) return TDM_ERR_INVALID_ARG;
+  if (h->general) return TDM_ERR_NOT_IMPLEMENTED;   // the adjoint of a nonsymmetric A is another matrix
   if (N < 0 || ld < N) return TDM_ERR_INVALID_ARG;
   if (N == 0) {
     DeviceGuard g(h->device);
@@ -204,6 +207,7 @@ extern "C" tdm_status tdm_get_info(tdm_handle h, tdm_info* info) {
   info->num_blocks = h->M;
   info->dominant = h->dominant;
   info->refine_steps = h->refine_steps;
+  info->general = h->general;
   info->max_abs_z = h->max_abs_z;
   info->min_abs_pivot = h->min_abs_pivot;
   info->device_error = err;

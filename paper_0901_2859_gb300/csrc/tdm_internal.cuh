@@ -36,7 +36,8 @@ enum {
   kStatSingular = 1,      // zero or tiny pivot, vanishing inverse-row diagonal
   kStatNotDominant = 2,   // some row violates |b_i| >= |a_{i-1}| + |a_i|
   kStatStrict = 4,        // some row satisfies it strictly
-  kStatNonFinite = 8
+  kStatNonFinite = 8,
+  kStatNotSymmetrizable = 16   // tdm_prepare_general: some sub[k] * sup[k] <= 0 or not finite
 };
 
 struct tdm_plan_s {
@@ -45,6 +46,7 @@ struct tdm_plan_s {
   int M = 0;               // number of blocks, M - 1 separators
   int refine_steps = 0;      // -1: tested per tile (cap 4); k > 0: exactly k corrections
   int tile_rhs = 0;          // right-hand sides per refined tile (0: by the shape rule)
+  int general = 0;           // 1: a nonsymmetric matrix, symmetrized (tdm_prepare_general)
   int dominant = 0;
   double max_abs_z = 0.0;
   double min_abs_pivot = 0.0;
@@ -55,7 +57,8 @@ struct tdm_plan_s {
   float* res32 = nullptr;     // [n][8]
   double* rR = nullptr;       // [M + 2]: rR[q] = Z^R_{p_q}(p_{q+1}), q = 1..M-2, else 0
   double* rL = nullptr;       // [M + 2]: rL[q] = Z^L_{p_q}(p_{q-1}), q = 2..M-1, else 0
-  double* a64 = nullptr;      // [max(n-1,1)] copy of a
+  double* a64 = nullptr;      // [max(n-1,1)] copy of a (general plans: the symmetrized off-diagonal)
+  double* tr = nullptr;       // [max(n-1,1)] general plans: t_{k+1} / t_k of the similarity T
   double* b64 = nullptr;      // [n] copy of b
   double* piv = nullptr;      // [4n] forward and backward pivots of A (double-double)
   unsigned long long* stat = nullptr;  // [8] device status / reductions

@@ -172,12 +172,33 @@ __device__ __forceinline__ void store_row(T* dst, const double* v) {
 }
 
 // One thread per block b.
+// Nonsymmetric A (Section 3.5): the similarity T = diag(t), t_{k+1} = t_k
+// (sub_k / sup_k)^(1/2), makes T^-1 A T symmetric with off-diagonal
+// sign(sup_k) (sub_k sup_k)^(1/2), provided every sub_k sup_k > 0.  Only the
+// ratios t_{k+1} / t_k are kept: the coefficients need t over one block at a
+// time, never its running product over the whole matrix.
+__global__ void k_symmetrize(const double* __restrict__ sub, const double* __restrict__ sup, int64_t n,
+                             double* __restrict__ ahat, double* __restrict__ tr, unsigned long long* stat) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n - 1;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double c = sub[k], a = sup[k], p = c * a;
+    if (!(p > 0.0) || !isfinite(p)) {
+      atomicOr(&stat[0], (unsigned long long)kStatNotSymmetrizable);
+      ahat[k] = 0.0;
+      tr[k] = 1.0;
+      continue;
+    }
+    ahat[k] = copysign(sqrt(p), a);
+    tr[k] = sqrt(c / a);
+  }
+}
+
 __global__ void k_block_coefficients(const double* __restrict__ a, const double* __restrict__ b,
                                      int64_t n, int t, int M,
                                      const dd* __restrict__ dF, const dd* __restrict__ dB,
                                      double* __restrict__ coef64, float* __restrict__ coef32,
                                      double* __restrict__ rR, double* __restrict__ rL,
-                                     unsigned long long* stat) {
+                                     const double* __restrict__ tr, unsigned long long* stat) {
   const int bidx = blockIdx.x * blockDim.x + threadIdx.x;
   if (bidx >= M) return;
   const double normA = __longlong_as_double((long long)stat[1]);
@@ -263,6 +284,37 @@ __global__ void k_block_coefficients(const double* __restrict__ a, const double*
     lf[0] = 0.0; invd[0] = 0.0; cc[0] = 0.0; phL[0] = 1.0; phR[0] = 0.0;
   }
 
+  // Nonsymmetric A = T S T^-1 with S the symmetric matrix above: x = A^-1 F =
+  // T S^-1 (T^-1 F).  Every factor of T folds into the coefficients as a ratio
+  // of t within this block (P[i] = t_i / t_lo, Q[i] = t_hi / t_i), so that the
+  // kernels solve A directly:
+  //   beta weights   gR *= t_hi / t_i,  gL *= t_lo / t_i
+  //   local sweep    lf *= t_i / t_{i-1},  cc *= t_i / t_{i+1}   (invd unchanged)
+  //   responses      phL *= t_i / t_lo,  phR *= t_i / t_hi
+  //   ratios         rR[q] *= t_hi / t_lo,  rL[q+1] *= t_lo / t_hi
+  // (the separator values are then those of x, not of T^-1 x).
+  if (tr) {
+    double P[65], Q[65];
+    const int nb = (int)(hi - lo);            // rows of the block
+    const int ext = has_right ? nb + 1 : nb;  // with the right separator row
+    P[0] = 1.0;
+    for (int k = 1; k < ext; k++) P[k] = P[k - 1] * tr[lo + k - 1];
+    Q[ext - 1] = 1.0;
+    for (int k = ext - 2; k >= 0; k--) Q[k] = Q[k + 1] * tr[lo + k];
+    for (int k = 0; k < nb; k++) {
+      const int64_t i = lo + k;
+      if (has_right) { gR[k] *= Q[k]; phR[k] /= Q[k]; }
+      if (has_left) { gL[k] /= P[k]; phL[k] *= P[k]; }
+      if (k > 0) lf[k] *= tr[i - 1];
+      if (i + 1 < n) cc[k] /= tr[i];
+    }
+    if (has_left && has_right) {
+      rR[bidx] *= Q[0];
+      rL[bidx + 1] /= Q[0];
+      zmax = fmax(fabs(rR[bidx]), fabs(rL[bidx + 1]));
+    }
+  }
+
   for (int64_t i = lo; i < hi; i++) {
     const int k = (int)(i - lo);
     double row[kNCOEF];
@@ -319,7 +371,7 @@ __global__ void k_residual_coefficients(const double* __restrict__ a, const doub
 static void tdm_free_plan(tdm_plan_s* p) {
   if (!p) return;
   cudaFree(p->coef64); cudaFree(p->coef32); cudaFree(p->res32);
-  cudaFree(p->rR); cudaFree(p->rL); cudaFree(p->a64); cudaFree(p->b64);
+  cudaFree(p->rR); cudaFree(p->rL); cudaFree(p->a64); cudaFree(p->b64); cudaFree(p->tr);
   cudaFree(p->piv); cudaFree(p->stat); cudaFree(p->dev_err);
   if (p->last) cudaEventDestroy(p->last);
   delete p;
@@ -396,12 +448,19 @@ tdm_status calibrate_refinement(tdm_plan_s* p, cudaStream_t s) {
 
 }  // namespace
 
-extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
-                                  const tdm_options* opt, void* stream, tdm_handle* out) {
+// The preparation of a symmetric matrix (a, b), or, with sub and sup, of a
+// nonsymmetric one: then a is unused and the symmetrized off-diagonal is
+// formed on the device.
+static tdm_status prepare_plan(const double* a, const double* b, const double* sub, const double* sup, int64_t n,
+                               const tdm_options* opt, void* stream, tdm_handle* out) {
   if (!out) return TDM_ERR_INVALID_ARG;
   *out = nullptr;
-  if (n < 1 || n > (int64_t(1) << 26) || !b || (n > 1 && !a)) return TDM_ERR_INVALID_ARG;
-  if (!tdm_aligned(b, 8) || (a && !tdm_aligned(a, 8))) return TDM_ERR_INVALID_ARG;
+  const bool general = sub != nullptr || sup != nullptr;
+  if (n < 1 || n > (int64_t(1) << 26) || !b) return TDM_ERR_INVALID_ARG;
+  if (general ? (n > 1 && (!sub || !sup)) : (n > 1 && !a)) return TDM_ERR_INVALID_ARG;
+  if (!tdm_aligned(b, 8) || (a && !tdm_aligned(a, 8)) || (sub && !tdm_aligned(sub, 8)) ||
+      (sup && !tdm_aligned(sup, 8)))
+    return TDM_ERR_INVALID_ARG;
   int t = 32, steps = 0, tile = 0;
   if (opt) {
     if (opt->flags != 0) return TDM_ERR_INVALID_ARG;
@@ -421,6 +480,7 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
   p->M = (int)((n + t - 1) / t);
   p->refine_steps = steps;
   p->tile_rhs = tile;
+  p->general = general ? 1 : 0;
   cudaGetDevice(&p->device);
   const int64_t na = n > 1 ? n - 1 : 1;
   bool ok = cudaMalloc(&p->coef64, sizeof(double) * n * kNCOEF) == cudaSuccess &&
@@ -430,6 +490,7 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
             cudaMalloc(&p->rL, sizeof(double) * (p->M + 2)) == cudaSuccess &&
             cudaMalloc(&p->a64, sizeof(double) * na) == cudaSuccess &&
             cudaMalloc(&p->b64, sizeof(double) * n) == cudaSuccess &&
+            (!general || cudaMalloc(&p->tr, sizeof(double) * na) == cudaSuccess) &&
             cudaMalloc(&p->piv, sizeof(dd) * 2 * n) == cudaSuccess &&
             cudaMalloc(&p->stat, sizeof(unsigned long long) * 8) == cudaSuccess &&
             cudaMalloc(&p->dev_err, sizeof(int)) == cudaSuccess &&
@@ -443,18 +504,22 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
   unsigned long long init[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   memcpy(&init[2], &inf, sizeof(double));
   cudaError_t e = cudaSuccess;
-  if (n > 1) e = cudaMemcpyAsync(p->a64, a, sizeof(double) * (n - 1), cudaMemcpyDeviceToDevice, s);
+  if (n > 1 && !general) e = cudaMemcpyAsync(p->a64, a, sizeof(double) * (n - 1), cudaMemcpyDeviceToDevice, s);
   else e = cudaMemsetAsync(p->a64, 0, sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->b64, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->stat, init, sizeof(init), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->rR, 0, sizeof(double) * (p->M + 2), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->rL, 0, sizeof(double) * (p->M + 2), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->dev_err, 0, sizeof(int), s);
+  if (e == cudaSuccess && general && n > 1)
+    k_symmetrize<<<(int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, s>>>(sub, sup, n, p->a64, p->tr,
+                                                                                          p->stat);
   if (e == cudaSuccess) {
     k_norm_and_dominance<<<64, 256, 0, s>>>(p->a64, p->b64, n, p->stat);
     k_pivots<<<2, kPivotThreads, 0, s>>>(p->a64, p->b64, n, reinterpret_cast<dd*>(p->piv), reinterpret_cast<dd*>(p->piv) + n, p->stat);
     k_block_coefficients<<<(p->M + 127) / 128, 128, 0, s>>>(
-        p->a64, p->b64, n, t, p->M, reinterpret_cast<dd*>(p->piv), reinterpret_cast<dd*>(p->piv) + n, p->coef64, p->coef32, p->rR, p->rL, p->stat);
+        p->a64, p->b64, n, t, p->M, reinterpret_cast<dd*>(p->piv), reinterpret_cast<dd*>(p->piv) + n, p->coef64, p->coef32, p->rR, p->rL,
+        general && n > 1 ? p->tr : nullptr, p->stat);
     k_residual_coefficients<<<(int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, s>>>(
         p->a64, p->b64, n, p->res32);
     e = cudaGetLastError();
@@ -468,6 +533,10 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
     return TDM_ERR_CUDA;
   }
   const unsigned flags = (unsigned)host_stat[0];
+  if (flags & kStatNotSymmetrizable) {   // Section 3.5 needs sub_k sup_k > 0
+    tdm_free_plan(p);
+    return TDM_ERR_INVALID_ARG;
+  }
   double normA, dmin, zmax;
   memcpy(&normA, &host_stat[1], sizeof(double));
   memcpy(&dmin, &host_stat[2], sizeof(double));
@@ -479,7 +548,7 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
     tdm_free_plan(p);
     return TDM_ERR_SINGULAR;
   }
-  if (steps == 0) {
+  if (steps == 0 && !general) {
     const tdm_status st = calibrate_refinement(p, s);
     if (st != TDM_OK) {
       tdm_free_plan(p);
@@ -488,4 +557,17 @@ extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
   }
   *out = p;
   return TDM_OK;
+}
+
+extern "C" tdm_status tdm_prepare(const double* a, const double* b, int64_t n,
+                                  const tdm_options* opt, void* stream, tdm_handle* out) {
+  return prepare_plan(a, b, nullptr, nullptr, n, opt, stream, out);
+}
+
+extern "C" tdm_status tdm_prepare_general(const double* sub, const double* diag, const double* sup, int64_t n,
+                                          const tdm_options* opt, void* stream, tdm_handle* out) {
+  if (n > 1 && (!sub || !sup)) return TDM_ERR_INVALID_ARG;
+  // n == 1 has no off-diagonal: a 1 x 1 general plan (sub, sup unused)
+  static const double kNone = 0.0;
+  return prepare_plan(nullptr, diag, n > 1 ? sub : &kNone, n > 1 ? sup : &kNone, n, opt, stream, out);
 }

@@ -64,6 +64,23 @@ def test_host_validation_rejects_bad_arguments(lib):
     assert lib.tdm_destroy(None) == 0
 
 
+def test_general_prepare_validation(lib):
+    from paper_0901_2859_gb300._lib import TDMOptions
+    h = ctypes.c_void_p()
+    # null diagonal, null off-diagonals with n > 1, n out of range: rejected before any CUDA call
+    assert lib.tdm_prepare_general(None, None, None, 10, None, None, ctypes.byref(h)) == 1
+    assert lib.tdm_prepare_general(None, ctypes.c_void_p(0x20000), ctypes.c_void_p(0x30000), 10, None, None,
+                                   ctypes.byref(h)) == 1
+    assert lib.tdm_prepare_general(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), ctypes.c_void_p(0x30000), 0,
+                                   None, None, ctypes.byref(h)) == 1
+    assert lib.tdm_prepare_general(ctypes.c_void_p(0x10004), ctypes.c_void_p(0x20000), ctypes.c_void_p(0x30000), 10,
+                                   None, None, ctypes.byref(h)) == 1   # misaligned
+    opt = TDMOptions(24, 0, 0, 0)
+    assert lib.tdm_prepare_general(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), ctypes.c_void_p(0x30000), 10,
+                                   ctypes.byref(opt), None, ctypes.byref(h)) == 1
+    assert h.value is None
+
+
 def test_bad_block_rows_rejected_before_any_cuda_call(lib):
     from paper_0901_2859_gb300._lib import TDMOptions
     h = ctypes.c_void_p()
