@@ -233,17 +233,12 @@ struct Cfg {
   size_t smem = 0;
 };
 
-int env_int(const char* name, int dflt) {
-  const char* v = getenv(name);
-  return v ? atoi(v) : dflt;
-}
-
 // binary32: 512 threads and at most ~111 KB of shared memory, so that two CTAs
 // (of different clusters) share an SM and one's exchange phase overlaps the
 // other's loads; binary64: 512 threads with 32 doubles per thread in registers.
 bool choose_cfg(int M, int t, bool fp64, Cfg& cfg) {
   const int maxt = 512;
-  const int pref = env_int(fp64 ? "TDM_R_FP64" : "TDM_R_FP32", fp64 ? 16 : 32);
+  const int pref = fp64 ? 16 : 32;   // the widest tile that fits; narrower ones for larger n
   for (int R = pref; R >= 8; R /= 2) {
     if (R != 8 && R != 16 && R != 32) continue;
     const int m_max = maxt / R;
@@ -331,8 +326,7 @@ tdm_status tdm_launch_plain(tdm_plan_s* p, const void* F, int64_t ldF, void* X, 
   const int tsize = fp64 ? 8 : 4;
   CUtensorMap map;
   memset(&map, 0, sizeof(map));
-  cfg.tma = env_int("TDM_NO_TMA", 0) == 0 &&
-            tdm_encode_tma_2d(&map, F, fp64, (uint64_t)N, (uint64_t)p->n, (uint64_t)ldF * tsize,
+  cfg.tma = tdm_encode_tma_2d(&map, F, fp64, (uint64_t)N, (uint64_t)p->n, (uint64_t)ldF * tsize,
                               (uint32_t)cfg.R, (uint32_t)cfg.box_rows);
   // the binary32 solve keeps its A4 arrays in the pair layout, sized for 512 / R blocks
   auto bytes = [&](bool tma) {
