@@ -151,6 +151,27 @@ tdm_status tdm_prepare_general(const double* sub, const double* diag, const doub
 tdm_status tdm_solve(tdm_handle h, const void* F, int64_t ldF, void* X, int64_t ldX,
                      int64_t N, tdm_precision prec, void* stream);
 
+/* tdm_solve_host -- tdm_solve for right-hand sides and solutions in HOST
+ * memory (no counterpart in the paper: the copies of a series that does not
+ * live on the device).  The columns are cut into chunks of `chunk` columns
+ * (0: about N/4, at least 2048; rounded up to a multiple of 16); each chunk is
+ * copied in, solved and copied out on separate streams, with two device
+ * staging buffers per direction that the plan keeps (sized for the largest
+ * chunk used), so that the copies overlap the solves.
+ *   F   host, [n][ldF], dtype per `prec`; X host, [n][ldX], dtype per `prec`.
+ *       Pinned memory lets the copies run asynchronously and overlap; pageable
+ *       memory works, with copies that the driver stages.
+ *   stream  all work starts after the work already enqueued on it, and the
+ *       stream completes when the last column of X has reached the host: the
+ *       caller synchronizes the stream before reading X.
+ * Calls on one plan must be ordered (one stream, or synchronized): they share
+ * the staging buffers.  Not capturable in a CUDA graph.
+ * Errors: TDM_ERR_INVALID_ARG (null or overlapping F and X, ld < N, chunk < 0),
+ * TDM_ERR_NOT_IMPLEMENTED (refined solve of a general plan; stream capture),
+ * TDM_ERR_NO_MEMORY, TDM_ERR_CUDA. */
+tdm_status tdm_solve_host(tdm_handle h, const void* F, int64_t ldF, void* X, int64_t ldX, int64_t N,
+                          int64_t chunk, tdm_precision prec, void* stream);
+
 /* tdm_solve_batched -- many distinct constant matrices, each with its own
  * block of right-hand sides (the per-mode series of the Fourier method,
  * Section 4, eqs. series_fft, poisson_end), in one persistent launch.

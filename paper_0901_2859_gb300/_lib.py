@@ -16,7 +16,7 @@ STATUS_NAMES = {
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_refined": 2}
 
 # every symbol include/tdm.h declares
-EXPORTS = ("tdm_prepare", "tdm_prepare_general", "tdm_solve", "tdm_solve_batched", "tdm_solve_batched_noalloc",
+EXPORTS = ("tdm_prepare", "tdm_prepare_general", "tdm_solve", "tdm_solve_host", "tdm_solve_batched", "tdm_solve_batched_noalloc",
            "tdm_solve_backward", "tdm_get_info", "tdm_destroy", "tdm_status_string")
 NOALLOC_MAX_TILES = 4096   # TDM_NOALLOC_MAX_TILES
 
@@ -63,6 +63,7 @@ def load(build_if_missing: bool = True):
         lib.tdm_prepare.argtypes = [vp, vp, i64, ctypes.POINTER(TDMOptions), vp, ctypes.POINTER(vp)]
         lib.tdm_prepare_general.argtypes = [vp, vp, vp, i64, ctypes.POINTER(TDMOptions), vp, ctypes.POINTER(vp)]
         lib.tdm_solve.argtypes = [vp, vp, i64, vp, i64, i64, i32, vp]
+        lib.tdm_solve_host.argtypes = [vp, vp, i64, vp, i64, i64, i64, i32, vp]
         lib.tdm_solve_batched.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                                           ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i64), i32, vp]
         lib.tdm_solve_batched_noalloc.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp),

@@ -103,6 +103,31 @@ class Plan:
         check(st, "tdm_solve")
         return out
 
+    def solve_host(self, F: torch.Tensor, precision: str = "fp32", out: torch.Tensor | None = None,
+                   chunk: int = 0) -> torch.Tensor:
+        """X = A^{-1} F for F and X in host memory (pin them for overlapped copies):
+        ``tdm_solve_host`` copies chunks of columns in, solves and copies them out on
+        separate streams.  Enqueued on the current stream; synchronize before reading X."""
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {list(PRECISIONS)}")
+        if not isinstance(F, torch.Tensor) or F.is_cuda:
+            raise TypeError("F must be a host (CPU) tensor")
+        if F.dtype != _IN_DTYPE[precision] or F.dim() != 2 or F.shape[0] != self.n or (F.shape[1] and F.stride(1) != 1):
+            raise ValueError(f"F must be a ({self.n}, N) {_IN_DTYPE[precision]} host tensor with unit column stride")
+        N = int(F.shape[1])
+        if out is None:
+            out = torch.empty((self.n, N), dtype=_OUT_DTYPE[precision], pin_memory=F.is_pinned())
+        if out.is_cuda or out.dtype != _OUT_DTYPE[precision] or tuple(out.shape) != (self.n, N) or \
+                (N and out.stride(1) != 1):
+            raise ValueError(f"out must be a ({self.n}, {N}) {_OUT_DTYPE[precision]} host tensor with unit column stride")
+        ldF, ldX = max(int(F.stride(0)), N), max(int(out.stride(0)), N)
+        with torch.cuda.device(self.device):
+            st = _lib.load().tdm_solve_host(self.handle, ctypes.c_void_p(F.data_ptr()), ldF,
+                                            ctypes.c_void_p(out.data_ptr()), ldX, N, int(chunk),
+                                            PRECISIONS[precision], _stream_ptr(self.device))
+        check(st, "tdm_solve_host")
+        return out
+
     def solve_backward(self, W: torch.Tensor, X: torch.Tensor, precision: str = "fp32",
                        need_ab: bool = True):
         """(dF, da, db) for L with dL/dX = W, X = A^{-1} F (adjoint solve, Lemma 2)."""

@@ -64,7 +64,10 @@ struct tdm_plan_s {
   unsigned long long* stat = nullptr;  // [8] device status / reductions
   int* dev_err = nullptr;     // [1] device error word of solves
   cudaEvent_t last = nullptr; // recorded after each solve
+  void* host_stage = nullptr; // staging buffers and streams of tdm_solve_host (created on first use)
 };
+
+void tdm_host_stage_free(void* stage);
 
 #define TDM_CUDA_TRY(expr)                                      \
   do {                                                          \

@@ -374,6 +374,7 @@ static void tdm_free_plan(tdm_plan_s* p) {
   cudaFree(p->rR); cudaFree(p->rL); cudaFree(p->a64); cudaFree(p->b64); cudaFree(p->tr);
   cudaFree(p->piv); cudaFree(p->stat); cudaFree(p->dev_err);
   if (p->last) cudaEventDestroy(p->last);
+  tdm_host_stage_free(p->host_stage);
   delete p;
 }
 

@@ -96,3 +96,8 @@ def test_bad_block_rows_rejected_before_any_cuda_call(lib):
     opt = TDMOptions(32, 9, 0, 0)
     assert lib.tdm_prepare(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), 100, ctypes.byref(opt),
                            None, ctypes.byref(h)) == 1
+
+
+def test_host_solve_validation(lib):
+    # rejected before any CUDA call: null handle, negative chunk, N < 0, bad precision
+    assert lib.tdm_solve_host(None, ctypes.c_void_p(0x1000), 4, ctypes.c_void_p(0x9000), 4, 4, 0, 2, None) == 1
