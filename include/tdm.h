@@ -229,6 +229,15 @@ tdm_status tdm_solve_backward(tdm_handle h, const void* W, const void* X, int64_
                               int64_t N, void* dF, double* da, double* db,
                               tdm_precision prec, void* stream);
 
+/* tdm_selftest_wait_timeout -- a check of the failure path of the solve
+ * kernels' bounded waits (no counterpart in the paper): one CTA waits on an
+ * mbarrier that nothing arrives at, gives up after `limit_cycles` clock
+ * cycles (1 .. 2^31), records the timeout in a device word and exits; the
+ * context stays usable.  Returns TDM_ERR_TIMEOUT when the wait gave up as it
+ * must, TDM_OK if it did not, TDM_ERR_INVALID_ARG for a limit out of range.
+ * Synchronizes the stream. */
+tdm_status tdm_selftest_wait_timeout(int64_t limit_cycles, void* stream);
+
 /* tdm_get_info -- plan properties and the device status of the last solve
  * (synchronizes with it). */
 tdm_status tdm_get_info(tdm_handle h, tdm_info* info);

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include "tdm_internal.cuh"
+#include "tdm_tma.cuh"
 
 tdm_status tdm_launch_plain(tdm_plan_s* p, const void* F, int64_t ldF, void* X, int64_t ldX,
                             int64_t N, bool fp64, cudaStream_t s);
@@ -93,7 +94,38 @@ __global__ void __launch_bounds__(256) k_grad_rows(const T* __restrict__ L, cons
   }
 }
 
+// A wait on an mbarrier that no thread arrives at: the bounded wait of the
+// solve kernels, with a caller-chosen limit, must give up and report.
+__global__ void k_wait_selftest(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) tdm_mbar_init(&bar, 1);
+  __syncthreads();
+  (void)tdm_mbar_wait(&bar, 0u, err, limit);
+}
+
 }  // namespace
+
+extern "C" tdm_status tdm_selftest_wait_timeout(int64_t limit_cycles, void* stream) {
+  if (limit_cycles < 1 || limit_cycles > (int64_t(1) << 31)) return TDM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  (void)cudaGetLastError();
+  int* d = nullptr;
+  TDM_CUDA_TRY(cudaMalloc(&d, sizeof(int)));
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 32, 0, s>>>(d, (long long)limit_cycles);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TDM_ERR_CUDA;
+  }
+  return h == kDevErrTmaTimeout ? TDM_ERR_TIMEOUT : TDM_OK;
+}
 
 // argument checks of tdm_solve, for the entry points defined in other files
 tdm_status tdm_validate_solve(const tdm_plan_s* h, const void* F, int64_t ldF, const void* X, int64_t ldX,

@@ -43,10 +43,10 @@ __device__ __forceinline__ void tdm_fence_proxy_async() {
 }
 
 // Wait for phase `parity` of the barrier.  Each try_wait may suspend the
-// thread for up to ~100 us until the phase completes; after ~2^31 clock
-// cycles (about a second) in total the wait gives up, records
-// kDevErrTmaTimeout and returns false.
-__device__ __forceinline__ bool tdm_mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+// thread for up to ~100 us until the phase completes; after `limit` clock
+// cycles in total (by default 2^31, about a second) the wait gives up,
+// records kDevErrTmaTimeout and returns false.
+__device__ __forceinline__ bool tdm_mbar_wait(uint64_t* bar, uint32_t parity, int* err, long long limit = 1ll << 31) {
   const uint32_t addr = tdm_smem_addr(bar);
   const long long t0 = clock64();
   while (true) {
@@ -57,7 +57,7 @@ __device__ __forceinline__ bool tdm_mbar_wait(uint64_t* bar, uint32_t parity, in
         : "r"(addr), "r"(parity), "r"(100000u)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > (1ll << 31)) {
+    if (clock64() - t0 > limit) {
       if (err) atomicExch(err, kDevErrTmaTimeout);
       return false;
     }

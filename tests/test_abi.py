@@ -101,3 +101,8 @@ def test_bad_block_rows_rejected_before_any_cuda_call(lib):
 def test_host_solve_validation(lib):
     # rejected before any CUDA call: null handle, negative chunk, N < 0, bad precision
     assert lib.tdm_solve_host(None, ctypes.c_void_p(0x1000), 4, ctypes.c_void_p(0x9000), 4, 4, 0, 2, None) == 1
+
+
+def test_selftest_limit_validation(lib):
+    assert lib.tdm_selftest_wait_timeout(0, None) == 1
+    assert lib.tdm_selftest_wait_timeout((1 << 31) + 1, None) == 1
