@@ -147,11 +147,15 @@ tdm_status tdm_prepare_general(const double* sub, const double* diag, const doub
  *       for TDM_FP32.  F and X must not overlap.
  *   N   number of right-hand sides; N == 0 is a no-op.
  * Pointers must be 16-byte aligned and ldF, ldX >= N.
- * Size limits: one thread-block cluster holds all n rows of a tile of
- * right-hand sides, so TDM_FP64 and TDM_FP32 solve n <= 32768 (32-row blocks;
- * 16384 with 16-row blocks) and TDM_FP32_REFINED n <= 65536; larger plans
- * return TDM_ERR_NOT_IMPLEMENTED from the solve (prepare accepts n <= 2^26).
- * Errors: TDM_ERR_INVALID_ARG, TDM_ERR_NOT_IMPLEMENTED (size limits), TDM_ERR_CUDA. */
+ * Sizes: one thread-block cluster holds all n rows of a tile of right-hand
+ * sides up to n = 1024 * block_rows (TDM_FP32_REFINED: 65536).  A larger
+ * symmetric plan is solved in two levels (Lemma 1 one level up): segments of
+ * at most 1024 * block_rows rows, each by a plan of its own, and the values at
+ * the rows between them from a reduced tridiagonal plan; X then takes one more
+ * read and write.  Batched refined solves (tdm_solve_batched with
+ * TDM_FP32_REFINED, tdm_solve_batched_noalloc) of such plans and general plans
+ * beyond the limit return TDM_ERR_NOT_IMPLEMENTED.
+ * Errors: TDM_ERR_INVALID_ARG, TDM_ERR_NOT_IMPLEMENTED, TDM_ERR_CUDA. */
 tdm_status tdm_solve(tdm_handle h, const void* F, int64_t ldF, void* X, int64_t ldX,
                      int64_t N, tdm_precision prec, void* stream);
 

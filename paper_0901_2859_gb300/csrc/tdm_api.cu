@@ -135,13 +135,17 @@ tdm_status tdm_validate_solve(const tdm_plan_s* h, const void* F, int64_t ldF, c
 
 tdm_status tdm_launch_solve(tdm_plan_s* p, const void* F, int64_t ldF, void* X, int64_t ldX,
                             int64_t N, tdm_precision prec, cudaStream_t s) {
+  tdm_status st = TDM_ERR_INVALID_ARG;
   switch (prec) {
-    case TDM_FP64: return tdm_launch_plain(p, F, ldF, X, ldX, N, true, s);
-    case TDM_FP32: return tdm_launch_plain(p, F, ldF, X, ldX, N, false, s);
+    case TDM_FP64: st = tdm_launch_plain(p, F, ldF, X, ldX, N, true, s); break;
+    case TDM_FP32: st = tdm_launch_plain(p, F, ldF, X, ldX, N, false, s); break;
     case TDM_FP32_REFINED:
-      return tdm_launch_refined(p, static_cast<const float*>(F), ldF, static_cast<double*>(X), ldX, N, s);
+      st = tdm_launch_refined(p, static_cast<const float*>(F), ldF, static_cast<double*>(X), ldX, N, s);
+      break;
   }
-  return TDM_ERR_INVALID_ARG;
+  // a plan beyond one cluster: the two-level solve (the direct kernels refuse before launching)
+  if (st == TDM_ERR_NOT_IMPLEMENTED && p->nseg > 0) st = tdm_launch_large(p, F, ldF, X, ldX, N, prec, s);
+  return st;
 }
 
 tdm_status tdm_launch_backward_sums(tdm_plan_s* p, const void* W, const void* X, int64_t ld,

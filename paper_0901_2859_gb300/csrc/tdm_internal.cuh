@@ -65,9 +65,21 @@ struct tdm_plan_s {
   int* dev_err = nullptr;     // [1] device error word of solves
   cudaEvent_t last = nullptr; // recorded after each solve
   void* host_stage = nullptr; // staging buffers and streams of tdm_solve_host (created on first use)
+  // two levels (n beyond one cluster, tdm_large.cu): segments, their plans, responses, reduced plan
+  int nseg = 0;
+  int64_t* seg_host = nullptr;     // [nseg + 1] segment starts (the separator after segment j is seg[j+1] - 1)
+  int64_t* seg_dev = nullptr;
+  double* phi = nullptr;           // [n][2] responses of every segment row to its left / right separator
+  tdm_plan_s** subs = nullptr;     // [nseg] the segments' plans
+  tdm_plan_s* reduced = nullptr;   // the separator values' plan (nseg - 1 rows)
 };
 
 void tdm_host_stage_free(void* stage);
+tdm_status tdm_prepare_large(tdm_plan_s* p, const double* a, const double* b, const tdm_options* opt,
+                             cudaStream_t s);
+void tdm_free_large(tdm_plan_s* p);
+tdm_status tdm_launch_large(tdm_plan_s* p, const void* F, int64_t ldF, void* X, int64_t ldX, int64_t N,
+                            tdm_precision prec, cudaStream_t s);
 
 #define TDM_CUDA_TRY(expr)                                      \
   do {                                                          \

@@ -375,6 +375,7 @@ static void tdm_free_plan(tdm_plan_s* p) {
   cudaFree(p->piv); cudaFree(p->stat); cudaFree(p->dev_err);
   if (p->last) cudaEventDestroy(p->last);
   tdm_host_stage_free(p->host_stage);
+  if (p->nseg > 0) tdm_free_large(p);
   delete p;
 }
 
@@ -552,6 +553,14 @@ static tdm_status prepare_plan(const double* a, const double* b, const double* s
   if (steps == 0 && !general) {
     const tdm_status st = calibrate_refinement(p, s);
     if (st != TDM_OK) {
+      tdm_free_plan(p);
+      return st;
+    }
+  }
+  if (!general && n > (int64_t)1024 * t) {   // beyond one cluster: the two-level structure
+    const tdm_status st = tdm_prepare_large(p, a, b, opt, s);
+    if (st != TDM_OK) {
+      (void)cudaGetLastError();
       tdm_free_plan(p);
       return st;
     }

@@ -191,9 +191,9 @@ def test_invalid_solve_arguments(tdm, dev):
 
 @pytest.mark.parametrize("precision,n_max", [("fp64", 32768), ("fp32", 32768)])
 def test_largest_supported_size_and_the_next(tdm, dev, oracle, precision, n_max):
-    """The largest n a cluster holds solves correctly (sampled columns against the
-    oracle); one more row is refused with TDM_ERR_NOT_IMPLEMENTED, not mis-solved."""
-    from paper_0901_2859_gb300 import TDMError, workloads
+    """The largest n a cluster holds solves correctly in one launch; one more row
+    takes the two-level scheme and solves correctly too."""
+    from paper_0901_2859_gb300 import workloads
     s = workloads.random_dominant(seed=7, n=n_max, N=24)
     plan = tdm.prepare(s.a, s.b, device=dev)
     dt = torch.float64 if precision == "fp64" else torch.float32
@@ -204,7 +204,7 @@ def test_largest_supported_size_and_the_next(tdm, dev, oracle, precision, n_max)
     plan.close()
     s2 = workloads.random_dominant(seed=8, n=n_max + 1, N=4)
     plan2 = tdm.prepare(s2.a, s2.b, device=dev)
-    with pytest.raises(TDMError) as e:
-        plan2.solve(torch.from_numpy(s2.F).to(dev, dt), precision)
-    assert e.value.status == 7
+    F2 = torch.from_numpy(s2.F).to(dev, dt)
+    X2 = plan2.solve(F2, precision).double().cpu().numpy()
+    assert relerr(X2, oracle.solve_hi(s2.a, s2.b, F2.double().cpu().numpy())) <= (1e-11 if precision == "fp64" else 2e-5)
     plan2.close()
