@@ -1,6 +1,6 @@
 // tdm_iface_df.cuh -- step A4 (separator values by Theorem 2, eq. theor_2)
-// for the refined solve, in binary32-pair ("double-float") arithmetic and in
-// logarithmic depth.
+// in logarithmic depth: in binary32-pair ("double-float") arithmetic for the
+// refined solve (PAIR = true), in binary32 for the plain binary32 solve.
 //
 // The separator values are x(p_j) = LR_j + LL_j + piR_j in_R + piL_j in_L
 // with the two first-order recurrences inside a CTA of m blocks
@@ -16,8 +16,12 @@
 //     first); level l adds to lane i the value of lane i -/+ 2^l times the
 //     product of the multipliers in between;
 //   - the partial sums of the other CTAs are folded in one round: every lane
-//     reads one CTA's total and multiplies it by the product of the
-//     multipliers of the CTAs in between; a shuffle tree adds them up.
+//     takes one CTA's total and multiplies it by the product of the
+//     multipliers of the CTAs in between; a shuffle tree adds them up.  The
+//     refined solve reads the totals remotely after a cluster barrier
+//     (iface_df_fold); the binary32 solve has every CTA push its totals into
+//     the others' shared memory, counted by an mbarrier (iface_push_send,
+//     iface_push_fold), with no cluster barrier.
 // A binary64 chain costs ~60 cycles per step on GB300 and the multipliers of
 // an ill-conditioned matrix are close to one, which is why the sums are kept
 // in pairs (~2^-46 relative) rather than in binary32.

@@ -21,12 +21,15 @@
 //            SL_q = beta^L_q     + rL_{q+1} SL_{q+1},    x(p_q) = SR_q + SL_q,
 //        because Z^R_{p_j}(p_i) = prod_{k=j}^{i-1} rR_k (a homogeneous solution
 //        restricted to [p_k, n) is a multiple of Z^R_{p_k}), and likewise for
-//        Z^L.  Each CTA runs both recurrences over its own blocks from zero in
-//        binary64 (LR, LL); the CTAs exchange one partial per direction through
-//        distributed shared memory; the incoming partials inR, inL enter as
-//        x(p_q) = LR_q + LL_q + piR_q inR + piL_q inL with prefix products
-//        piR, piL of the ratios.  This is the GPU form of the dichotomy's
-//        level-by-level schedule (Algorithm 4): depth O(m + C), O(M) work.
+//        Z^L.  Each CTA runs both recurrences over its own blocks from zero
+//        (LR, LL): sequentially in binary64 for the binary64 solve, as warp
+//        scans in binary32 (tdm_iface_df.cuh) for the binary32 solve; the CTAs
+//        exchange one partial per direction through distributed shared memory
+//        (binary64: remote loads after a cluster barrier; binary32: pushed with
+//        st.async and counted by an mbarrier); the incoming partials inR, inL
+//        enter as x(p_q) = LR_q + LL_q + piR_q inR + piL_q inL with prefix
+//        products piR, piL of the ratios.  This is the GPU form of the
+//        dichotomy's level-by-level schedule (Algorithm 4): O(M) work.
 //  A5    back substitution of the local sweep and the correction
 //        x_i = y_i + phiL_i x(p_b) + phiR_i x(p_{b+1}); one coalesced store.
 // F is read once and X written once per tile.
