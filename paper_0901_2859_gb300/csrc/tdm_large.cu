@@ -69,25 +69,30 @@ __global__ void k_reduced_rhs(const double* __restrict__ a, const int64_t* __res
   }
 }
 
-template <typename TX, typename TR>
+// X's arithmetic type throughout: binary32 X is combined in binary32 (the
+// binary64 pipe runs at 1/64 of the binary32 rate on GB300), binary64 X in
+// binary64
+template <typename TX>
 __global__ void k_combine(const int64_t* __restrict__ seg, int K, int64_t n, const double* __restrict__ phi,
-                          const TR* __restrict__ Xs, int64_t N, TX* __restrict__ X, int64_t ldX) {
+                          const TX* __restrict__ Xs, int64_t N, TX* __restrict__ X, int64_t ldX) {
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     // segment of row i (K is small: a linear scan of the boundaries)
     int j = 0;
     while (j + 1 < K && i >= seg[j + 1]) j++;
     const bool sep = (j + 1 < K) && (i == seg[j + 1] - 1);
-    const double pl = (j > 0 && !sep) ? phi[2 * i] : 0.0;
-    const double pr = (j + 1 < K && !sep) ? phi[2 * i + 1] : 0.0;
+    const TX pl = (TX)((j > 0 && !sep) ? phi[2 * i] : 0.0);
+    const TX pr = (TX)((j + 1 < K && !sep) ? phi[2 * i + 1] : 0.0);
+    const TX* xl = Xs + (int64_t)(j > 0 ? j - 1 : 0) * N;
+    const TX* xr = Xs + (int64_t)j * N;
     TX* row = X + i * ldX;
     for (int64_t c = threadIdx.x; c < N; c += blockDim.x) {
       if (sep) {
-        row[c] = (TX)Xs[(int64_t)j * N + c];
+        row[c] = xr[c];
       } else {
-        double x = (double)row[c];
-        if (j > 0) x = fma(pl, (double)Xs[(int64_t)(j - 1) * N + c], x);
-        if (j + 1 < K) x = fma(pr, (double)Xs[(int64_t)j * N + c], x);
-        row[c] = (TX)x;
+        TX x = row[c];
+        if (j > 0) x = fma(pl, xl[c], x);
+        if (j + 1 < K) x = fma(pr, xr[c], x);
+        row[c] = x;
       }
     }
   }
@@ -212,11 +217,11 @@ tdm_status tdm_launch_large(tdm_plan_s* p, const void* F, int64_t ldF, void* X, 
   if (st == TDM_OK) {
     const int gc = (int)std::min<int64_t>(n, 8192);
     if (prec == TDM_FP32)
-      k_combine<float, float><<<gc, 256, 0, s>>>(p->seg_dev, K, n, p->phi, static_cast<const float*>(Xs), N,
-                                                 static_cast<float*>(X), ldX);
+      k_combine<float><<<gc, 256, 0, s>>>(p->seg_dev, K, n, p->phi, static_cast<const float*>(Xs), N,
+                                          static_cast<float*>(X), ldX);
     else
-      k_combine<double, double><<<gc, 256, 0, s>>>(p->seg_dev, K, n, p->phi, static_cast<const double*>(Xs), N,
-                                                   static_cast<double*>(X), ldX);
+      k_combine<double><<<gc, 256, 0, s>>>(p->seg_dev, K, n, p->phi, static_cast<const double*>(Xs), N,
+                                           static_cast<double*>(X), ldX);
     if (cudaGetLastError() != cudaSuccess) st = TDM_ERR_CUDA;
   }
   cudaFreeAsync(R, s);
