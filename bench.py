@@ -443,6 +443,53 @@ def run_adi(args):
         print(json.dumps(line), flush=True)
 
 
+def run_large(args):
+    """A series beyond one cluster (n = 262144, N = 1024): the two-level solve,
+    in every precision, with sampled columns checked against the oracle."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_0901_2859_gb300 as tdm
+
+    dev = torch.device("cuda", DIST["local"])
+    torch.cuda.set_device(dev)
+    n, N, s_shift = 262144, 1024, 1e-6
+    a = -np.ones(n - 1)
+    b = np.full(n, 2.0 + s_shift)
+    rng = np.random.default_rng(DIST["rank"])
+    F32 = torch.from_numpy(rng.standard_normal((n, N), dtype=np.float32)).to(dev)
+    t0 = time.perf_counter()
+    plan = tdm.prepare(a, b, device=dev)
+    torch.cuda.synchronize()
+    prepare_s = time.perf_counter() - t0
+    paths = {}
+    cols = np.array([0, 1, N // 2, N - 1])
+    for prec, Fin, dt_out, bytes_per in (("fp32_refined", F32, torch.float64, 12), ("fp64", F32.double(), torch.float64, 16),
+                                         ("fp32", F32, torch.float32, 8)):
+        X = torch.empty((n, N), dtype=dt_out, device=dev)
+        steps = max(3, min(args.steps, 20))
+        ms = _events_time(lambda: plan.solve(Fin, prec, out=X), steps, args.warmup, torch)
+        ref = oracle.solve_hi(a, b, Fin[:, cols].double().cpu().numpy())
+        err = float(np.max(np.abs(X[:, cols].double().cpu().numpy() - ref)) / np.max(np.abs(ref)))
+        hbm, _ = _peaks()
+        paths[prec] = {"ms": ms, "unknowns_per_s": n * N / (ms * 1e-3), "rel_err_sampled": err,
+                       "hbm_frac_algorithmic": n * N * bytes_per / (ms * 1e-3) / 1e9 / hbm}
+        del X
+    info = plan.info()
+    plan.close()
+    line = {
+        "metric": "unknowns solved/s beyond one cluster (two-level solve)", "value": paths["fp32_refined"]["unknowns_per_s"],
+        "unit": UNIT, "n_gpus": DIST["world"], "steps": max(3, min(args.steps, 20)), "warmup": args.warmup,
+        "ms_per_step": paths["fp32_refined"]["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"large: n={n} N={N} s={s_shift} (a=-1, b=2+s), F~N(0,1) fp32; segments of 32768 rows",
+                   "n": n, "N": N, "refine_steps": info["refine_steps"]},
+        "paths": paths, "prepare_s": prepare_s,
+    }
+    if DIST["rank"] == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The oracle (the plain CPU implementation), timed on the host cores on a bounded sample."""
     N_RHS = args.rhs
@@ -487,9 +534,10 @@ def main():
     ap.add_argument("--cpu-cols", type=int, default=8192, help="columns of the CPU baseline sample")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline: seconds of repeated passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "poisson2d", "adi"],
+    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "poisson2d", "adi", "large"],
                     help="precision: the benchmark line; batching: 512 matrices of uneven size in one launch; "
-                         "poisson2d: the Fourier method on a 1024 x 1024 mesh, 100 problems; adi: alternating directions")
+                         "poisson2d: the Fourier method on a 1024 x 1024 mesh, 100 problems; adi: alternating directions; "
+                         "large: the two-level solve beyond one cluster")
     ap.add_argument("--rhs", type=int, default=N_RHS,
                     help="right-hand sides of the series (the benchmark is 8192; smaller values are for profiling)")
     args = ap.parse_args()
@@ -497,6 +545,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "large":
+        run_large(args)
     elif args.workload == "adi":
         run_adi(args)
     elif args.workload == "poisson2d":

@@ -108,3 +108,16 @@ def test_adi_reaches_eps_against_the_fourier_solution(N):
     # a planted mistake (omega scaled by h^2 twice) does not converge
     bad = op.peaceman_rachford(fr, N, op.adi_parameters(N, eps) / N ** 2)
     assert np.max(np.abs(bad - ref)) > 100 * eps * np.max(np.abs(ref))
+
+
+def test_product_sine_transform_on_cpu():
+    """The package's FFT-based type-I sine transform (plain torch, runs on CPU too)
+    equals the oracle's explicit sine sums."""
+    import torch
+    from paper_0901_2859_gb300.poisson import dst1
+    x = np.random.default_rng(11).standard_normal((4, 29, 3))
+    got = dst1(torch.from_numpy(x), dim=1).numpy()
+    ref = np.einsum("lj,ijn->iln", op.sine_matrix(30), x)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    got0 = dst1(torch.from_numpy(x[:, :, 0].T.copy()), dim=0).numpy()
+    assert np.allclose(got0, ref[:, :, 0].T, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
