@@ -22,6 +22,7 @@ numpy part (this file):
   z_vectors             Z^R_k, Z^L_k from eq. z_vector (for the Theorem 4 bound)
   explicit_inverse      the explicit inverse of Section 3.6 (eqs. x1-x3),
                         symmetric case
+  algorithm2            selected solution components as G_k^T F (Algorithm 2, Section 3.1)
   thomas_general        the sweep for a general (nonsymmetric) tridiagonal matrix
   symmetrizer           the diagonal similarity that symmetrizes it (Section 3.5)
 Parity is pinned for every function here by ``tests/test_oracle_pins.py``.
@@ -400,3 +401,17 @@ def symmetrizer(sub, sup):
     for k in range(sub.shape[0]):
         t[k + 1] = t[k] * np.sqrt(sub[k] / sup[k])
     return t
+
+
+def algorithm2(a, b, F, ks):
+    """Algorithm 2: the components k of every solution, X[k, :] = G_k^T F with
+    A G_k = e_k (G_k by the binary64 sweep, then a plain matrix product).
+    Returns an array of shape (len(ks), N)."""
+    a, b = _f64(a), _f64(b)
+    F, _ = _as2d(F)
+    n = b.shape[0]
+    ks = np.asarray(ks, dtype=np.int64)
+    E = np.zeros((n, ks.size))
+    E[ks, np.arange(ks.size)] = 1.0
+    G = thomas_f64(a, b, E)          # columns G_k
+    return G.T @ F

@@ -321,3 +321,20 @@ def test_symmetrizer_section_3_5(oracle):
     t_bad = 1.0 / t
     S_bad = np.diag(1.0 / t_bad) @ A @ np.diag(t_bad)
     assert np.max(np.abs(S_bad - S_bad.T)) > 1e-3
+
+
+def test_algorithm2_components_equal_the_full_solve(oracle):
+    """Algorithm 2 (X_k = G_k^T F, A G_k = e_k) gives the same components as the
+    full solve; with every k it is the explicit inverse applied to F."""
+    n, N = 300, 7
+    rng = np.random.default_rng(21)
+    a = -0.5 - 0.5 * rng.random(n - 1)
+    b = 2.5 + rng.random(n)
+    F = rng.standard_normal((n, N))
+    ks = [0, 1, 57, 150, n - 2, n - 1]
+    ref = oracle.solve_hi(a, b, F)[ks]
+    got = oracle.algorithm2(a, b, F, ks)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    full = oracle.algorithm2(a[:39], b[:40], F[:40], np.arange(40))
+    dense = np.linalg.solve(oracle.dense(a[:39], b[:40]), F[:40])
+    assert np.max(np.abs(full - dense)) <= 1e-13 * np.max(np.abs(dense))
