@@ -490,6 +490,49 @@ def run_large(args):
         print(json.dumps(line), flush=True)
 
 
+def run_algorithm2(args):
+    """Algorithm 2 (Section 3.1) at the benchmark size: every separator value of
+    the precision series (P = M - 1 = 511 components) as G^T F, in binary64 and
+    as three TF32 tensor-core products; the dichotomy's own separator values are
+    the reference."""
+    import numpy as np
+    import torch
+    import paper_0901_2859_gb300 as tdm
+    from paper_0901_2859_gb300 import workloads
+    from paper_0901_2859_gb300.algorithm2 import components, inverse_rows
+
+    dev = torch.device("cuda", DIST["local"])
+    torch.cuda.set_device(dev)
+    n, N = N_ROWS, 8192
+    s = workloads.precision(seed=0, n=n, N=N, s=SHIFT)
+    plan = tdm.prepare(s.a, s.b, device=dev)
+    t = plan.info()["block_rows"]
+    ks = list(range(t, n, t))                      # the separator rows
+    F = torch.from_numpy(s.F).to(dev)
+    ref = plan.solve(F.double(), "fp64")[ks]
+    steps = max(3, min(args.steps, 10))
+    G = inverse_rows(plan, ks)
+    ms_g = _events_time(lambda: inverse_rows(plan, ks), steps, 3, torch)
+    out = {}
+    for mode in ("tf32x3", "fp64"):
+        ms = _events_time(lambda: components(plan, F, ks, mode, G=G), steps if mode == "tf32x3" else 3, 3, torch)
+        X = components(plan, F, ks, mode, G=G).double()
+        err = float(((X - ref).abs().amax(dim=1) / ref.abs().amax(dim=1)).max())
+        flops = 2.0 * len(ks) * n * N * (3 if mode == "tf32x3" else 1)
+        out[mode] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12, "rel_err_vs_dichotomy": err}
+    plan.close()
+    line = {
+        "metric": "separator values by Algorithm 2 (dense G^T F)", "value": out["tf32x3"]["ms"], "unit": "ms",
+        "n_gpus": DIST["world"], "steps": steps, "warmup": 3, "ms_per_step": out["tf32x3"]["ms"],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
+        "config": {"workload": f"algorithm2: precision series n={n} N={N}, {len(ks)} separator components",
+                   "components": len(ks)},
+        "paths": out, "inverse_rows_ms": ms_g,
+    }
+    if DIST["rank"] == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The oracle (the plain CPU implementation), timed on the host cores on a bounded sample."""
     N_RHS = args.rhs
@@ -534,10 +577,10 @@ def main():
     ap.add_argument("--cpu-cols", type=int, default=8192, help="columns of the CPU baseline sample")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline: seconds of repeated passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "poisson2d", "adi", "large"],
+    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "poisson2d", "adi", "large", "algorithm2"],
                     help="precision: the benchmark line; batching: 512 matrices of uneven size in one launch; "
                          "poisson2d: the Fourier method on a 1024 x 1024 mesh, 100 problems; adi: alternating directions; "
-                         "large: the two-level solve beyond one cluster")
+                         "large: the two-level solve beyond one cluster; algorithm2: separator values as dense products")
     ap.add_argument("--rhs", type=int, default=N_RHS,
                     help="right-hand sides of the series (the benchmark is 8192; smaller values are for profiling)")
     args = ap.parse_args()
@@ -545,6 +588,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "algorithm2":
+        run_algorithm2(args)
     elif args.workload == "large":
         run_large(args)
     elif args.workload == "adi":
