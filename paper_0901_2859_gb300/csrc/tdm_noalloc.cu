@@ -104,6 +104,18 @@ extern "C" tdm_status tdm_solve_batched_noalloc(const tdm_handle* hs, int count,
     if (st != TDM_OK) return st;
     if (hs[k]->device != hs[0]->device || hs[k]->t != hs[0]->t) return TDM_ERR_INVALID_ARG;
   }
+  // Not capturable: a captured copy from g_stage would re-read the host array
+  // at every replay, after later calls have refilled it.  Refused before
+  // anything is staged or enqueued.
+  {
+    CurrentDevice guard(hs[0]->device);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return TDM_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return TDM_ERR_NOT_IMPLEMENTED;
+  }
   std::lock_guard<std::mutex> lock(g_mu);
 
   // the work list's size, checked against the array before anything is enqueued
@@ -152,7 +164,9 @@ extern "C" tdm_status tdm_solve_batched_noalloc(const tdm_handle* hs, int count,
   if (st != TDM_OK) return st;
   // From pageable host memory: the call returns once g_stage has been copied
   // out, so the next call may refill it; the device copy is stream-ordered
-  // after this stream's earlier launches that read g_tiles.
+  // after this stream's earlier launches that read g_tiles.  The driver may
+  // stage such a copy synchronously: the call can then block the host until
+  // the stream's earlier work has finished.
   TDM_CUDA_TRY(cudaMemcpyAsync(d_tiles, g_stage, sizeof(RefItem) * (size_t)nitems, cudaMemcpyHostToDevice, s));
   for (int i = 0; i < ne;) {
     int j = i, off = 0;
@@ -163,9 +177,6 @@ extern "C" tdm_status tdm_solve_batched_noalloc(const tdm_handle* hs, int count,
     if (st != TDM_OK) return st;
     i = j;
   }
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  TDM_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
-  if (cs == cudaStreamCaptureStatusNone)
-    for (int k = 0; k < count; k++) TDM_CUDA_TRY(cudaEventRecord(hs[k]->last, s));
+  for (int k = 0; k < count; k++) TDM_CUDA_TRY(cudaEventRecord(hs[k]->last, s));
   return TDM_OK;
 }

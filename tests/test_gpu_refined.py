@@ -49,7 +49,7 @@ def test_refined_edge_sizes(tdm, dev, oracle, n, block_rows):
 
 @pytest.mark.parametrize("N", [1, 5, 16, 17, 40, 64])
 def test_refined_ragged_rhs_counts_and_alignment(tdm, dev, oracle, N):
-    """N = 16, 40 and 64 take the TMA-staged path; the others the direct-load path."""
+    """Column counts below, at and between multiples of the tile width (ragged last tiles)."""
     from paper_0901_2859_gb300 import workloads
     s = workloads.plain_fp64(seed=N, n=2000, N=N)
     F32 = s.F.astype(np.float32)

@@ -109,14 +109,15 @@ def test_poisson2d_fp64_closed_form_and_oracle(tdm, dev, oracle):
     ks = s.meta["pure_modes"][:12]
     Fe, Xe, lam = oracle.eigen_closed_form(n, s.b[0], ks)
     Xm = plan.solve(torch.from_numpy(Fe).to(dev), "fp64").cpu().numpy()
-    kappa = 4.0 / lam.min()
+    # (an exactly rounded input mode is not an exact eigenvector: its rounding
+    # is amplified by lambda_k / lambda_min, which only the high modes feel)
     for c in range(len(ks)):
-        tol = max(1e-11, 10 * U64 * lam[c] / lam.min(), 10 * U64 * kappa)
+        tol = max(1e-11, 10 * U64 * lam[c] / lam.min())
         assert relerr(Xm[:, c], Xe[:, c]) <= tol
-    # mixed columns against the oracle (sampled)
+    # pure-mode and mixed columns against the oracle: the binary64 gate, 1e-11
     cols = np.r_[0:8, 64:72, n - 8:n]
     ref = oracle.solve_hi(s.a, s.b, s.F[:, cols])
-    assert relerr(X[:, cols], ref) <= max(1e-11, 10 * U64 * kappa)
+    assert relerr(X[:, cols], ref) <= 1e-11
     # binary32 on the mode + noise columns (on pure high modes at kappa ~ 3.4e6 the
     # binary32 inverse rows alone cost ~1e-3: reported by the benchmark, not gated)
     cols = np.r_[64:72, n - 8:n]

@@ -106,3 +106,55 @@ def test_capacity_limit(env, oracle):
     ora = oracle.solve_hi(a, b, F[:, cols].cpu().numpy().astype(np.float64))
     assert relerr(Xf[:, cols].cpu().numpy(), ora) <= TOL
     plan.close()
+
+
+TDM_ERR_NOT_IMPLEMENTED = 7
+
+
+def test_refused_under_stream_capture(env):
+    """Under stream capture the call returns TDM_ERR_NOT_IMPLEMENTED and enqueues
+    nothing: a captured copy of the host-side work list would be re-read at every
+    replay, after later calls have refilled it."""
+    tdm, lib, dev = env
+    _, plans, Fs = _batch(tdm, dev, seed=23, count=3, n_min=100, n_max=3000, N_max=20)
+    outs = _nan_outs(plans, Fs, dev)
+    marker = torch.zeros(4, device=dev)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        marker.add_(1.0)                            # the graph is not empty
+        status = _call(lib, plans, Fs, outs, dev)
+    assert status == TDM_ERR_NOT_IMPLEMENTED
+    graph.replay()
+    torch.cuda.synchronize()
+    assert all(torch.isnan(x).all() for x in outs)  # no solve was captured
+    assert float(marker[0]) == 1.0
+    for p in plans:
+        p.close()
+
+
+def test_calls_on_two_streams_ordered_by_an_event(env, oracle):
+    """Call A on one stream, an event makes a second stream wait for it, call B
+    (which overwrites the shared work list) on the second stream: both right."""
+    tdm, lib, dev = env
+    sA, pA, FA = _batch(tdm, dev, seed=24, count=5, n_min=64, n_max=5000, N_max=30)
+    sB, pB, FB = _batch(tdm, dev, seed=25, count=6, n_min=300, n_max=9000, N_max=50)
+    outA, outB = _nan_outs(pA, FA, dev), _nan_outs(pB, FB, dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    s1.wait_stream(torch.cuda.current_stream(dev))
+    s2.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s1):
+        assert _call(lib, pA, FA, outA, dev) == 0
+    done_a = torch.cuda.Event()
+    done_a.record(s1)
+    s2.wait_event(done_a)
+    with torch.cuda.stream(s2):
+        assert _call(lib, pB, FB, outB, dev) == 0
+    torch.cuda.synchronize()
+    for series, outs in ((sA, outA), (sB, outB)):
+        for s, x in zip(series, outs):
+            xn = x.cpu().numpy()
+            assert np.isfinite(xn).all()
+            assert relerr(xn, oracle.solve_hi(s.a, s.b, s.F.astype(np.float64))) <= TOL
+    for p in pA + pB:
+        p.close()
