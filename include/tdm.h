@@ -80,16 +80,18 @@ typedef struct {
   int block_rows;    /* rows per block (the paper's subvector size); 0 = automatic (32).
                         Allowed: 16 or 32. */
   int refine_steps;  /* TDM_FP32_REFINED corrections:
-                          k in 1..4: exactly k;
-                          -1: every tile of right-hand sides tests its own: at least two, then
-                              stop once the estimated relative error
-                              max|d_k|^2 / (max|x| max|d_{k-1}|) of the last correction is
-                              below 1e-12; at most 4 (device_error 2 otherwise);
-                          0 (automatic): tdm_prepare solves 64 seeded right-hand sides with the
-                              per-tile test and fixes the plan's count to the most corrections
-                              any tile needed; -1 if that reached the cap or the plan is too
-                              large to calibrate cheaply (n > ~350000 uses fewer columns,
-                              n > ~2.8e6 none).  tdm_info reports the result. */
+                          k in 1..4: exactly k, no test;
+                          -1: every tile of right-hand sides tests its own corrections: after
+                              the first, stop if its size max|d_1| / max|x| times the plan's
+                              contraction is below 2.5e-12; after the k-th (k >= 2), stop if the
+                              estimated relative error max|d_k|^2 / (max|x| max|d_{k-1}|) is
+                              below 1e-12; at most 4 (device_error 2 otherwise).  Requested
+                              explicitly, the contraction is 1 (at least two corrections);
+                          0 (automatic): -1 with the contraction measured by tdm_prepare on 64
+                              seeded right-hand sides (four corrections: twice the size of the
+                              second per unit of the first).  Plans too large to calibrate cheaply
+                              (n > ~350000 uses fewer columns, n > ~2.8e6 none) keep contraction 1.
+                              tdm_info reports both. */
   int flags;         /* reserved, must be 0 */
   int tile_rhs;      /* TDM_FP32_REFINED: right-hand sides per tile of the solve kernel, 4, 8 or
                         16; 0 (automatic) = 8 where the shape fits (the shape rule falls back to
@@ -110,6 +112,8 @@ typedef struct {
                               before the convergence test passed) */
   int32_t tile_rhs;        /* the plan's tile_rhs option (0 = automatic) */
   int32_t general;         /* 1 for a plan of tdm_prepare_general (a nonsymmetric matrix) */
+  float contraction;       /* TDM_FP32_REFINED per-tile test: estimated relative error left by
+                              the first correction per unit of its size (1 = not calibrated) */
 } tdm_info;
 
 /* tdm_prepare -- Algorithm 3/4, step 1 (Sections 3.3-3.4; eqs. green_v, z_vector).

@@ -31,7 +31,8 @@ class TDMInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("block_rows", ctypes.c_int32), ("num_blocks", ctypes.c_int32),
                 ("dominant", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("max_abs_z", ctypes.c_double), ("min_abs_pivot", ctypes.c_double),
-                ("device_error", ctypes.c_int32), ("tile_rhs", ctypes.c_int32), ("general", ctypes.c_int32)]
+                ("device_error", ctypes.c_int32), ("tile_rhs", ctypes.c_int32), ("general", ctypes.c_int32),
+                ("contraction", ctypes.c_float)]
 
 
 class TDMError(RuntimeError):

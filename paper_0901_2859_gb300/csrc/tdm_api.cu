@@ -243,6 +243,7 @@ extern "C" tdm_status tdm_get_info(tdm_handle h, tdm_info* info) {
   info->num_blocks = h->M;
   info->dominant = h->dominant;
   info->refine_steps = h->refine_steps;
+  info->contraction = h->contraction;
   info->general = h->general;
   info->max_abs_z = h->max_abs_z;
   info->min_abs_pivot = h->min_abs_pivot;

@@ -70,6 +70,7 @@ tdm_status build(WorkList* w, tdm_plan_s* const* ps, int count, const void* cons
   std::vector<Entry> es;
   for (int k = 0; k < count; k++) {
     if (N[k] == 0) continue;
+    if (ldF[k] > kRefMaxLd || ldX[k] > kRefMaxLd) return TDM_ERR_NOT_IMPLEMENTED;
     RefShape sh;
     if (!tdm_refined_shape(ps[k]->M, ps[k]->t, ps[k]->tile_rhs, sh)) return TDM_ERR_NOT_IMPLEMENTED;
     es.push_back({k, sh, (double)ps[k]->n * (double)N[k]});

@@ -274,7 +274,10 @@ __device__ __forceinline__ void iface_df_setup(const IfaceDF<R, MM, PAIR>& f, co
 
 // LR_j, LL_j of this CTA and its totals (into xch[parity]); one warp scans a
 // column in both directions.  The betas must be visible (CTA barrier).
-template <int R, int MM, bool PAIR = true>
+// AP: the arithmetic of the scan -- pairs, or binary32 on the leading words of
+// the same storage (a correction solve of the refined path needs only binary32
+// separator values).
+template <int R, int MM, bool PAIR = true, bool AP = PAIR>
 __device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM, PAIR>& f, int m, int parity) {
   constexpr int RP = IfaceDF<R, MM, PAIR>::kRP;
   constexpr int KMAX = (MM + 31) / 32;   // most blocks per lane (1: every lane holds one block)
@@ -285,29 +288,29 @@ __device__ __forceinline__ void iface_df_scan(const IfaceDF<R, MM, PAIR>& f, int
     // in-lane sequential parts (stored, then completed with what enters the lane)
     f2pair accR{0.f, 0.f}, accL{0.f, 0.f};
     for (int j = j0; j < j1; j++) {
-      accR = mfma<PAIR>(mld<PAIR>(&f.aR()[j]), accR, f2pair{f.beR()[j * RP + r], 0.f});
+      accR = mfma<AP>(mld<AP>(&f.aR()[j]), accR, f2pair{f.beR()[j * RP + r], 0.f});
       if (KMAX > 1 && K > 1) f.st_lr((j + 1) * RP + r, accR);
     }
     for (int j = j1 - 1; j >= j0; j--) {
-      accL = mfma<PAIR>(mld<PAIR>(&f.aL()[j]), accL, f2pair{f.beL()[j * RP + r], 0.f});
+      accL = mfma<AP>(mld<AP>(&f.aL()[j]), accL, f2pair{f.beL()[j * RP + r], 0.f});
       if (KMAX > 1 && K > 1) f.st_ll(j * RP + r, accL);
     }
 #pragma unroll
     for (int l = 0; l < 5; l++) {
       const int d = 1 << l;
-      const f2pair pR = mshfl_up<PAIR>(accR, d);
-      const f2pair pL = mshfl_down<PAIR>(accL, d);
-      if (lane >= d && lane < nl) accR = mfma<PAIR>(mld<PAIR>(&f.ksR()[l * 32 + lane]), pR, accR);
-      if (lane + d < nl) accL = mfma<PAIR>(mld<PAIR>(&f.ksL()[l * 32 + lane]), pL, accL);
+      const f2pair pR = mshfl_up<AP>(accR, d);
+      const f2pair pL = mshfl_down<AP>(accL, d);
+      if (lane >= d && lane < nl) accR = mfma<AP>(mld<AP>(&f.ksR()[l * 32 + lane]), pR, accR);
+      if (lane + d < nl) accL = mfma<AP>(mld<AP>(&f.ksL()[l * 32 + lane]), pL, accL);
     }
     if (KMAX > 1 && K > 1) {
-      f2pair eR = mshfl_up<PAIR>(accR, 1);     // everything left of this lane
-      f2pair eL = mshfl_down<PAIR>(accL, 1);   // everything right of it
+      f2pair eR = mshfl_up<AP>(accR, 1);     // everything left of this lane
+      f2pair eL = mshfl_down<AP>(accL, 1);   // everything right of it
       if (lane == 0) eR = f2pair{0.f, 0.f};
       if (lane + 1 >= nl) eL = f2pair{0.f, 0.f};
       for (int j = j0; j < j1; j++) {
-        f.st_lr((j + 1) * RP + r, mfma<PAIR>(mld<PAIR>(&f.cpR()[j]), eR, f.ld_lr((j + 1) * RP + r)));
-        f.st_ll(j * RP + r, mfma<PAIR>(mld<PAIR>(&f.cpL()[j]), eL, f.ld_ll(j * RP + r)));
+        f.st_lr((j + 1) * RP + r, mfma<AP>(mld<AP>(&f.cpR()[j]), eR, f.ld_lr((j + 1) * RP + r)));
+        f.st_ll(j * RP + r, mfma<AP>(mld<AP>(&f.cpL()[j]), eL, f.ld_ll(j * RP + r)));
       }
     } else if (j0 < m) {   // one block per lane: the scan already holds the values
       f.st_lr((j0 + 1) * RP + r, accR);
@@ -378,7 +381,7 @@ __device__ __forceinline__ void iface_push_fold(const IfaceDF<R, MM, false>& f, 
 // in_R, in_L of every column from the other CTAs' totals (after a cluster
 // barrier): one warp per column, lanes 0-15 for the CTAs to the left, 16-31
 // for those to the right.
-template <int R, int MM, bool PAIR = true>
+template <int R, int MM, bool PAIR = true, bool AP = PAIR>
 __device__ __forceinline__ void iface_df_fold(const IfaceDF<R, MM, PAIR>& f, int C, unsigned c, int parity) {
   const int lane = threadIdx.x & 31, cc = lane & 15;
   const bool left = lane < 16;
@@ -387,22 +390,28 @@ __device__ __forceinline__ void iface_df_fold(const IfaceDF<R, MM, PAIR>& f, int
     f2pair v{0.f, 0.f};
     if (valid) {
       const float2 x = ld_cluster_f32x2(f.xch() + (parity * 2 + (left ? 0 : 1)) * R + r, (unsigned)cc);
-      v = mfma<PAIR>(mld<PAIR>(left ? &f.wR()[cc] : &f.wL()[cc]), fp(x), f2pair{0.f, 0.f});
+      v = mfma<AP>(mld<AP>(left ? &f.wR()[cc] : &f.wL()[cc]), fp(x), f2pair{0.f, 0.f});
     }
 #pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) v = madd<PAIR>(v, mshfl_xor<PAIR>(v, o));
+    for (int o = 8; o >= 1; o >>= 1) v = madd<AP>(v, mshfl_xor<AP>(v, o));
     if (lane == 0) f.in()[r] = f2(v);
     if (lane == 16) f.in()[R + r] = f2(v);
   }
 }
 
-// x(p_j) for column r, rounded to binary32
-template <int R, int MM, bool PAIR = true>
-__device__ __forceinline__ float iface_df_sep(const IfaceDF<R, MM, PAIR>& f, int j, int r) {
+// x(p_j) for column r, as a pair (AP) or a binary32 value in .h
+template <int R, int MM, bool PAIR = true, bool AP = PAIR>
+__device__ __forceinline__ f2pair iface_df_sep_pair(const IfaceDF<R, MM, PAIR>& f, int j, int r) {
   constexpr int RP = IfaceDF<R, MM, PAIR>::kRP;
-  f2pair x = madd<PAIR>(f.ld_lr(j * RP + r), f.ld_ll(j * RP + r));
-  x = mfma<PAIR>(mld<PAIR>(&f.piR()[j]), mld<PAIR>(&f.in()[r]), x);
-  x = mfma<PAIR>(mld<PAIR>(&f.piL()[j]), mld<PAIR>(&f.in()[R + r]), x);
+  f2pair x = madd<AP>(f.ld_lr(j * RP + r), f.ld_ll(j * RP + r));
+  x = mfma<AP>(mld<AP>(&f.piR()[j]), mld<AP>(&f.in()[r]), x);
+  x = mfma<AP>(mld<AP>(&f.piL()[j]), mld<AP>(&f.in()[R + r]), x);
+  return x;
+}
+// x(p_j) for column r, rounded to binary32
+template <int R, int MM, bool PAIR = true, bool AP = PAIR>
+__device__ __forceinline__ float iface_df_sep(const IfaceDF<R, MM, PAIR>& f, int j, int r) {
+  const f2pair x = iface_df_sep_pair<R, MM, PAIR, AP>(f, j, r);
   return x.h + x.l;
 }
 

@@ -45,6 +45,7 @@ struct tdm_plan_s {
   int t = 0;               // rows per block
   int M = 0;               // number of blocks, M - 1 separators
   int refine_steps = 0;      // -1: tested per tile (cap 4); k > 0: exactly k corrections
+  float contraction = 1.f;   // per-tile test: error after one correction ~ its size x this (1: untested)
   int tile_rhs = 0;          // right-hand sides per refined tile (0: by the shape rule)
   int general = 0;           // 1: a nonsymmetric matrix, symmetrized (tdm_prepare_general)
   int dominant = 0;
@@ -55,6 +56,7 @@ struct tdm_plan_s {
   double* coef64 = nullptr;   // [n][8]
   float* coef32 = nullptr;    // [n][8]
   float* res32 = nullptr;     // [n][8]
+  float* rtab = nullptr;      // [M + 1][kRefTabStride(t)] coefficient table of the refined kernel (tdm_refine.cuh)
   double* rR = nullptr;       // [M + 2]: rR[q] = Z^R_{p_q}(p_{q+1}), q = 1..M-2, else 0
   double* rL = nullptr;       // [M + 2]: rL[q] = Z^L_{p_q}(p_{q-1}), q = 2..M-1, else 0
   double* a64 = nullptr;      // [max(n-1,1)] copy of a (general plans: the symmetrized off-diagonal)

@@ -126,6 +126,7 @@ extern "C" tdm_status tdm_solve_batched_noalloc(const tdm_handle* hs, int count,
     Entry e;
     e.k = k;
     e.t = hs[k]->t;
+    if (ldF[k] > kRefMaxLd || ldX[k] > kRefMaxLd) return TDM_ERR_NOT_IMPLEMENTED;
     if (!tdm_refined_shape(hs[k]->M, e.t, hs[k]->tile_rhs, e.sh)) return TDM_ERR_NOT_IMPLEMENTED;
     const int64_t tiles = (N[k] + e.sh.R - 1) / e.sh.R;
     total += tiles;

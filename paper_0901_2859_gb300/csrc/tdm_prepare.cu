@@ -366,11 +366,62 @@ __global__ void k_residual_coefficients(const double* __restrict__ a, const doub
   }
 }
 
+// The refined kernel's coefficient table (tdm_refine.cuh): every coefficient
+// of rows j and j + t/2 side by side, phi also as a binary32 pair (its second
+// word is phi - (float)phi, exact to binary64 rounding).
+__global__ void k_refined_table(const double* __restrict__ coef64, const float* __restrict__ res32, int64_t n,
+                                int t, int M, float* __restrict__ tab) {
+  const int H = t / 2;
+  const int64_t total = (int64_t)(M + 1) * (H + 1);   // H row pairs and the rest of every block
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(k / (H + 1)), j = (int)(k % (H + 1));
+    float* blk = tab + (size_t)b * kRefTabStride(t);
+    const int64_t row0 = (int64_t)b * t;
+    if (j == H) {   // the local sweep row by row, and a of the row before the block
+      for (int i = 0; i < t; i++) {
+        const int64_t row = row0 + i;
+        const bool ok = b < M && row < n;
+        blk[kRefLF(t) + i] = ok ? (float)coef64[row * kNCOEF + kLF] : 0.f;
+        const int w = t - 1 - i;   // the substitution's step that visits row i
+        blk[kRefCI(t) + 2 * w] = ok ? (float)coef64[row * kNCOEF + kC] : 0.f;
+        blk[kRefCI(t) + 2 * w + 1] = ok ? (float)coef64[row * kNCOEF + kINVD] : 0.f;
+      }
+      const int64_t prev = row0 - 1;
+      const bool ok = b < M && prev >= 0 && prev < n;
+      blk[kRefTail(t) + 0] = ok ? res32[prev * kNRES + kA0] : 0.f;
+      blk[kRefTail(t) + 1] = ok ? res32[prev * kNRES + kA1] : 0.f;
+      blk[kRefTail(t) + 2] = 0.f;
+      blk[kRefTail(t) + 3] = 0.f;
+      continue;
+    }
+    float v[kRefTP];
+    for (int q = 0; q < kRefTP; q++) v[q] = 0.f;
+    for (int h = 0; h < 2; h++) {
+      const int64_t i = row0 + j + h * H;
+      if (b >= M || i >= n) continue;
+      const double* cr = coef64 + i * kNCOEF;
+      const float* rr = res32 + i * kNRES;
+      v[kRT_GR + h] = (float)cr[kGR];
+      v[kRT_GL + h] = (float)cr[kGL];
+      const float plh = (float)cr[kPHIL], prh = (float)cr[kPHIR];
+      v[kRT_PLH + h] = plh;
+      v[kRT_PRH + h] = prh;
+      v[kRT_PLL + h] = (float)(cr[kPHIL] - (double)plh);
+      v[kRT_PRL + h] = (float)(cr[kPHIR] - (double)prh);
+      v[kRT_S0 + h] = rr[kS0];
+      v[kRT_S1 + h] = rr[kS1];
+      v[kRT_A0 + h] = rr[kA0];
+      v[kRT_A1 + h] = rr[kA1];
+    }
+    for (int q = 0; q < kRefTP; q++) blk[j * kRefTP + q] = v[q];
+  }
+}
+
 }  // namespace
 
 static void tdm_free_plan(tdm_plan_s* p) {
   if (!p) return;
-  cudaFree(p->coef64); cudaFree(p->coef32); cudaFree(p->res32);
+  cudaFree(p->coef64); cudaFree(p->coef32); cudaFree(p->res32); cudaFree(p->rtab);
   cudaFree(p->rR); cudaFree(p->rL); cudaFree(p->a64); cudaFree(p->b64); cudaFree(p->tr);
   cudaFree(p->piv); cudaFree(p->stat); cudaFree(p->dev_err);
   if (p->last) cudaEventDestroy(p->last);
@@ -394,11 +445,19 @@ extern "C" tdm_status tdm_destroy(tdm_handle h) {
 
 // ---------------------------------------------------------------------------
 // Automatic refinement (refine_steps = 0): one solve of seeded right-hand sides
-// with the per-tile test fixes the number of corrections of the plan to the
-// most that any tile needed.  The contraction of a correction is a property
-// of the matrix and of the binary32 solve, so later solves can skip the
-// cluster-wide test.  Plans too large for a cheap calibration, and matrices
-// whose calibration does not converge within the cap, keep the per-tile test.
+// with kRefineCalibSteps corrections records the size of every correction,
+// max over columns of max|d_k| / max|x|.  Convergence is fast (each correction
+// shrinks the error by the binary32 solve's relative accuracy), so the size of
+// correction 2 per unit of correction 1 is the contraction of one correction:
+// a property of the matrix and of the binary32 solve more than of F.  The plan
+// then tests every tile of right-hand sides after its first correction with
+// that contraction (estimated error = size of the first correction x the
+// contraction, kept twice as large as measured) and after later ones with the
+// ratio test (tdm_refine.cu).  Right-hand sides like the calibration's stop
+// after one correction; ones whose first solve is far less accurate relative
+// to their solution (pure high modes of an ill-conditioned matrix) take more.
+// Plans too large for a cheap calibration keep contraction 1: at least two
+// corrections per tile.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -424,18 +483,20 @@ tdm_status calibrate_refinement(tdm_plan_s* p, cudaStream_t s) {
   float* F = nullptr;
   double* X = nullptr;
   tdm_status st = TDM_OK;
-  int h_used = 0, h_err = 0;
+  int h_err = 0;
+  float ratios[kRefineCalibSteps] = {0.f, 0.f, 0.f, 0.f};
   if (cudaMalloc(&F, sizeof(float) * p->n * N) != cudaSuccess || cudaMalloc(&X, sizeof(double) * p->n * N) != cudaSuccess) {
     st = TDM_ERR_NO_MEMORY;
   } else {
-    st = tdm_corrections_counter(true, nullptr, s);
+    st = tdm_calibration_record(true, nullptr, s);
     cudaError_t e = cudaSuccess;
     if (st == TDM_OK) {
       k_calib_rhs<<<128, 256, 0, s>>>(F, p->n * N, 0x9e3779b9u);
-      const RefItem one = tdm_refined_item(p, F, N, X, N, N, 0);
+      RefItem one = tdm_refined_item(p, F, N, X, N, N, 0);
+      one.steps = kRefineCalib;
       st = tdm_refined_launch(sh, p->t, nullptr, &one, (N + sh.R - 1) / sh.R, p->dev_err, s);
     }
-    if (st == TDM_OK) st = tdm_corrections_counter(false, &h_used, s);
+    if (st == TDM_OK) st = tdm_calibration_record(false, ratios, s);
     if (st == TDM_OK) e = cudaMemcpyAsync(&h_err, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (st == TDM_OK && e == cudaSuccess) e = cudaMemsetAsync(p->dev_err, 0, sizeof(int), s);
     if (st == TDM_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -444,7 +505,11 @@ tdm_status calibrate_refinement(tdm_plan_s* p, cudaStream_t s) {
   if (F) cudaFree(F);
   if (X) cudaFree(X);
   (void)cudaGetLastError();
-  if (st == TDM_OK && h_err == 0 && h_used >= 1 && h_used < 4) p->refine_steps = h_used;
+  // ratios[k]: the size of correction k + 1
+  if (st == TDM_OK && h_err == 0 && ratios[0] > 0.f && ratios[1] < ratios[0])
+    p->contraction = 2.f * ratios[1] / ratios[0];
+  else if (st == TDM_OK && h_err == 0 && ratios[0] == 0.f)
+    p->contraction = 0.f;   // the first solve was exact on the calibration columns
   return st;
 }
 
@@ -488,6 +553,7 @@ static tdm_status prepare_plan(const double* a, const double* b, const double* s
   bool ok = cudaMalloc(&p->coef64, sizeof(double) * n * kNCOEF) == cudaSuccess &&
             cudaMalloc(&p->coef32, sizeof(float) * n * kNCOEF) == cudaSuccess &&
             cudaMalloc(&p->res32, sizeof(float) * n * kNRES) == cudaSuccess &&
+            cudaMalloc(&p->rtab, sizeof(float) * (size_t)(p->M + 1) * kRefTabStride(t)) == cudaSuccess &&
             cudaMalloc(&p->rR, sizeof(double) * (p->M + 2)) == cudaSuccess &&
             cudaMalloc(&p->rL, sizeof(double) * (p->M + 2)) == cudaSuccess &&
             cudaMalloc(&p->a64, sizeof(double) * na) == cudaSuccess &&
@@ -524,6 +590,11 @@ static tdm_status prepare_plan(const double* a, const double* b, const double* s
         general && n > 1 ? p->tr : nullptr, p->stat);
     k_residual_coefficients<<<(int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, s>>>(
         p->a64, p->b64, n, p->res32);
+    {
+      const int64_t rows = (int64_t)(p->M + 1) * (t / 2 + 1);
+      k_refined_table<<<(int)((rows + 255) / 256 < 1024 ? (rows + 255) / 256 : 1024), 256, 0, s>>>(
+          p->coef64, p->res32, n, t, p->M, p->rtab);
+    }
     e = cudaGetLastError();
   }
   unsigned long long host_stat[8];

@@ -6,20 +6,31 @@
 // Work items.  An item is one tile of R right-hand sides of one series
 // A X = F.  A thread-block cluster processes one item at a time with all n rows
 // (CTA c owns m blocks of t rows, thread (block, rhs) owns one block for one
-// right-hand side) and walks a list of items; consecutive items of a cluster
-// normally belong to the same series.  Per item:
+// right-hand side) and walks a list of items.  Per item:
 //
-//   x  = solve32(F)                                   (steps A2-A5, binary32)
-//   repeat (adaptive, at most 4 times, or a fixed count):
-//     r_i = F_i - (A x)_i                             (error-free, see below)
-//     x  += solve32(r)
-//   X_i = xh_i + xl_i rounded once to binary64.
+//   x   = solve(F)          binary32 sweeps and beta sums (Lemma 1, eq.
+//                           beta_symn), separator values by Theorem 2 in
+//                           binary32 pairs, and the block interiors
+//                           x = y + phiL x(p_b) + phiR x(p_{b+1}) formed with
+//                           phi and the separator values as pairs: x is kept
+//                           as a pair (xh, xl) carrying no binary32 rounding
+//   r   = F - A x           error-free binary32 transformations (below)
+//   d   = solve(r)          all binary32 (separator values too)
+//   X   = xh + xl + d       rounded once to binary64
 //
-// x is held as x0 + delta: x0, the first solve's binary32 result, in
-// registers; delta, the sum of the corrections, in shared memory, updated with
-// an exact TwoSum whose rounding error is carried to the output.  F is read
-// from global memory for the first solve and again (from L2) for each
-// residual, so shared memory holds no copy of the tile.
+// One correction is enough at condition numbers of several million: the first
+// solve's error is then its smooth part alone (~4e-7 of max|x| at kappa ~ 4e6,
+// from the binary32 beta sums), and the correction solve recovers that to its
+// own relative accuracy.  Had x been rounded to binary32, the residual would be
+// dominated by that rounding (~2^-24 |A| |x|, a rough vector) and the
+// correction, whose beta sums see the rough part through binary32 inverse rows,
+// would stall near 1e-10.  More corrections (refine_steps > 1, the per-tile
+// test, the prepare-time calibration) repeat the residual and the correction.
+//
+// Rows of a block are held as pairs (row j, row j + t/2) in float2 registers:
+// the two halves of a block run through the beta sums, the residual, the
+// corrections and the output in lockstep on paired binary32 instructions
+// (tdm_f2.cuh); only the sweeps' recurrences walk the rows one at a time.
 //
 // The residual is formed in row-sum form.  With sigma_i = b_i + a_{i-1} + a_i
 // and the fluxes E_i = a_i (x_{i+1} - x_i),
@@ -38,26 +49,31 @@
 #include <map>
 #include <mutex>
 #include <tuple>
-#include <vector>
 
 #include "tdm_df.cuh"
+#include "tdm_f2.cuh"
 #include "tdm_iface_df.cuh"
 #include "tdm_kernel_common.cuh"
 #include "tdm_refine.cuh"
 #include "tdm_tma.cuh"
 
-// Most corrections any tile of a per-tile-tested launch has made on this
-// device since the counter was last cleared (read by the prepare-time
-// calibration; concurrent launches can only raise it).
-__device__ int g_tdm_corrections_max;
+// Calibration record: for corrections k = 1..kRefineCalibSteps of calibration
+// solves, the largest max|d_k| / max|x| over columns and tiles (binary32 bit
+// patterns of non-negative values, which order like unsigned integers).
+__device__ unsigned g_tdm_calib[kRefineCalibSteps];
 
 namespace {
 using namespace tdmk;
 
-// Estimated relative error left after a correction d_k: ratio_k^2 / ratio_{k-1}
-// (linear convergence), with ratio_k = max over columns of max|d_k| / max|x|;
-// after the first correction, ratio_1 itself.
+// Per-tile test (refine_steps = -1), with ratio_k = max over the tile's columns
+// of max|d_k| / max|x|: after the first correction, stop once ratio_1 times the
+// plan's contraction (measured at prepare: the error left after one correction
+// per unit of its size) is below kRefineTol1; after correction k >= 2, once
+// the estimated relative error ratio_k^2 / ratio_{k-1} (linear convergence) is
+// below kRefineTol.
 constexpr float kRefineTol = 1e-12f;
+constexpr float kRefineTol1 = 2.5e-12f;
+constexpr int kRefineCap = 4;
 
 // max over columns of (max|d| / max|x|) over the whole cluster; every thread of
 // every CTA gets the same value (exact maxima, the same division).  slot holds
@@ -84,7 +100,7 @@ __device__ __forceinline__ float cluster_ratio(const float* slot, int C, int tid
   return *bcast;
 }
 
-// per-CTA, per-column maxima of |d| and |x0| into slot [2][R]: shuffles over
+// per-CTA, per-column maxima of |d| and |x| into slot [2][R]: shuffles over
 // the blocks a warp covers, then over the warps
 template <int R>
 __device__ __forceinline__ void cta_maxima(float md, float mx, float* red, float* slot, int tid) {
@@ -110,215 +126,303 @@ __device__ __forceinline__ void cta_maxima(float md, float mx, float* red, float
   }
 }
 
-// streaming loads/stores for the right-hand sides and the solution: they are
-// touched once per tile and must not evict the coefficients from L1
+// Loads of F and stores of X.  A thread's rows are the rows of its block in
+// one column, addressed by 32-bit element offsets from the block's first row
+// (the launch requires ld <= kRefMaxLd), each load and store predicated on
+// its row's existence (no branch).  Both stream: the data is touched once per
+// tile and must not evict the coefficients from L1.
 __device__ __forceinline__ float ld_stream(const float* p) {
   float v;
   asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
   return v;
 }
+__device__ __forceinline__ float ld_stream_if(const float* p, bool pred) {
+  float v;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\tmov.f32 %0, 0f00000000;\n\t"
+      "@q ld.global.nc.L1::no_allocate.f32 %0, [%1];\n\t}"
+      : "=f"(v) : "l"(p), "r"((int)pred));
+  return v;
+}
 __device__ __forceinline__ void st_stream(double* p, double v) {
   asm volatile("st.global.cs.f64 [%0], %1;" ::"l"(p), "d"(v));
 }
-__device__ __forceinline__ void ldg4(const float* p, float& x, float& y, float& z, float& w) {
-  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-  x = v.x; y = v.y; z = v.z; w = v.w;
+__device__ __forceinline__ void st_stream_if(double* p, double v, bool pred) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.global.cs.f64 [%0], %1;\n\t}"
+               ::"l"(p), "d"(v), "r"((int)pred));
 }
 
-// 4 coefficients from shared memory (SM = true) or through the read-only cache
+// Where a thread's rows of F (or X) are and which exist: base = the block's
+// first row in the thread's column, ld32 = the row stride, rows = how many of
+// the block's rows exist in this column (0 for padding threads).
+template <typename T>
+struct Rows {
+  T* base;
+  int ld32;
+  int rows;
+  __device__ __forceinline__ T* at(int i) const { return base + i * ld32; }
+};
+
+// F of rows j and j + t/2, or zeros where the rows do not exist
+template <int TT>
+__device__ __forceinline__ float2 load_pair(const Rows<const float>& f, int j) {
+  constexpr int H = TT / 2;
+  return make_float2(ld_stream_if(f.at(j), j < f.rows), ld_stream_if(f.at(j + H), j + H < f.rows));
+}
+template <int TT>
+__device__ __forceinline__ void load_rhs(float2 (&g)[TT / 2], const Rows<const float>& f) {
+#pragma unroll
+  for (int j = 0; j < TT / 2; j++) g[j] = load_pair<TT>(f, j);
+}
+
+// Exact binary32 -> binary64 by rebuilding the bit pattern on the integer
+// pipe (the conversion instruction runs at the binary64 rate on GB300), no
+// branch: zeros keep their sign, infinities and NaNs stay so.  A subnormal
+// input is read as 2^-127 (1 + f) instead of 2^-126 f: only the low word of a
+// pair can be one, and then only below 2^-126, under the last bit of any
+// solution entry above ~2^-100.
+__device__ __forceinline__ double f2d_bits(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t a = u & 0x7fffffffu;
+  uint32_t hi = (a >> 3) + 0x38000000u;        // exponent rebiased by 1023 - 127
+  hi = a >= 0x7f800000u ? hi + 0x38000000u : hi;   // Inf, NaN: the exponent all ones
+  hi = a == 0u ? 0u : hi;
+  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(u << 29));
+}
+// X = hi + lo rounded once to binary64: hi exactly, lo exactly unless it is
+// subnormal (then |lo| < 2^-126, far below the last bit of any hi > 2^-100)
+__device__ __forceinline__ double pair_to_f64(float hi, float lo) { return f2d_bits(hi) + f2d_bits(lo); }
+
+// coefficient table reads: shared memory (SM) or the read-only cache
 template <bool SM>
-__device__ __forceinline__ void cld4(const float* p, float& x, float& y, float& z, float& w) {
-  if constexpr (SM) ld4(p, x, y, z, w);
-  else ldg4(p, x, y, z, w);
+__device__ __forceinline__ float tld1(const float* p) {
+  if constexpr (SM) return *p;
+  else return __ldg(p);
+}
+template <bool SM>
+__device__ __forceinline__ float2 tld2(const float* p) {
+  if constexpr (SM) return *reinterpret_cast<const float2*>(p);
+  else return __ldg(reinterpret_cast<const float2*>(p));
+}
+template <bool SM>
+__device__ __forceinline__ float4 tld4(const float* p) {
+  if constexpr (SM) return *reinterpret_cast<const float4*>(p);
+  else return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// this thread's low words of x: a float2 {row j, row j + t/2} per j
+__device__ __forceinline__ float2 ldxl(const float* xlp, int j) { return reinterpret_cast<const float2*>(xlp)[j]; }
+__device__ __forceinline__ void stxl(float* xlp, int j, float2 v) { reinterpret_cast<float2*>(xlp)[j] = v; }
+
+// row i of the block in the pair registers
+template <int H>
+__device__ __forceinline__ float& at(float2 (&g)[H], int i) {
+  return i < H ? g[i].x : g[i - H].y;
 }
 
-// forward pass (A2 + A3)
-template <int TT, bool FULL, bool SM>
-__device__ __forceinline__ void forward_pass_g(float (&v)[TT], const float* cf, int nrows, float& bR, float& bL) {
-  float g = 0.f;
+// A2 + A3: the beta sums over the block (paired rows), then the forward
+// elimination of the local sweep, row by row (g replaced by its result)
+template <int TT, bool SM>
+__device__ __forceinline__ void forward_pass(float2 (&g)[TT / 2], const float* cb, float& bR, float& bL) {
+  constexpr int H = TT / 2;
+  float2 sR = make_float2(0.f, 0.f), sL = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int i = 0; i < TT; i++) {
-    if (FULL || i < nrows) {
-      float gr, gl, lf, unused;
-      cld4<SM>(cf + i * kNCOEF, gr, gl, lf, unused);
-      bR = fmaf(gr, v[i], bR);
-      bL = fmaf(gl, v[i], bL);
-      g = fmaf(-lf, g, v[i]);
-      v[i] = g;
-    }
+  for (int j = 0; j < H; j++) {
+    const float4 w = tld4<SM>(cb + j * kRefTP + kRT_GR);
+    sR = f2fma(lo2(w), g[j], sR);
+    sL = f2fma(hi2(w), g[j], sL);
+  }
+  bR = sR.x + sR.y;
+  bL = sL.x + sL.y;
+  float e = 0.f;
+#pragma unroll
+  for (int i = 0; i < TT; i += 4) {
+    const float4 lf = tld4<SM>(cb + kRefLF(TT) + i);
+    e = fmaf(-lf.x, e, at<H>(g, i));
+    at<H>(g, i) = e;
+    e = fmaf(-lf.y, e, at<H>(g, i + 1));
+    at<H>(g, i + 1) = e;
+    e = fmaf(-lf.z, e, at<H>(g, i + 2));
+    at<H>(g, i + 2) = e;
+    e = fmaf(-lf.w, e, at<H>(g, i + 3));
+    at<H>(g, i + 3) = e;
   }
 }
 
-// F of one block for one right-hand side (zero outside the system)
-template <int TT, bool FULL>
-__device__ __forceinline__ void load_rhs(float (&g)[TT], const float* Fp, int64_t ldF, bool active, int nrows) {
-  if (active) {
+// A5, first part: the back substitution of the local sweep (independent of the
+// separator values), y replaces g
+template <int TT, bool SM>
+__device__ __forceinline__ void backward_y(float2 (&g)[TT / 2], const float* cb) {
+  constexpr int H = TT / 2;
+  float y = 0.f;
 #pragma unroll
-    for (int i = 0; i < TT; i++) {
-      g[i] = (FULL || i < nrows) ? ld_stream(Fp) : 0.f;
-      Fp += ldF;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < TT; i++) g[i] = 0.f;
+  for (int w = 0; w < TT; w += 2) {   // rows TT-1-w and TT-2-w
+    const float4 ci = tld4<SM>(cb + kRefCI(TT) + 2 * w);   // (off-diagonal, 1 / pivot) of both rows
+    y = fmaf(-ci.x, y, at<H>(g, TT - 1 - w)) * ci.y;
+    at<H>(g, TT - 1 - w) = y;
+    y = fmaf(-ci.z, y, at<H>(g, TT - 2 - w)) * ci.w;
+    at<H>(g, TT - 2 - w) = y;
   }
 }
 
-// Residual r = F - A x of the iterate x = x0 + delta over one block, in
-// row-sum form: r_i = F_i - sigma_i x_i + E_{i-1} - E_i with the fluxes
-// E_i = a_i (x_{i+1} - x_i).  g holds F on entry and r on exit.  FIRST: delta
-// is still zero (first correction), so the differences of x are single
-// TwoSums and sigma x a pair-by-float product.  Rows past n carry zero
-// coefficients, F and x, so they add nothing.  The rows are done in two parts
-// so that the interior (rows 1 .. TT-2, this block's iterate only) can run
-// while the cluster barrier that publishes the neighbours' edge values
-// completes; rows 0 and TT-1 follow.
-
-// r_i from F_i, the fluxes on both sides of row i and sigma_i x_i (the large
-// fluxes cancel exactly in the first TwoSum)
-__device__ __forceinline__ float residual_row(float Fi, f2pair Ep, f2pair E, f2pair S) {
-  const f2pair w = two_sum_f(Ep.h, -E.h);
-  const f2pair u = two_sum_f(Fi, w.h);
-  const f2pair v = two_sum_f(u.h, -S.h);
-  const float small = ((Ep.l - E.l) - S.l) + (w.l + u.l + v.l);
-  return v.h + small;
-}
-template <bool FIRST>
-__device__ __forceinline__ f2pair x_diff(f2pair x1, f2pair x0) {
-  if constexpr (FIRST) return two_sum_f(x1.h, -x0.h);
-  else return df_diff(x1, x0);
-}
-template <bool FIRST>
-__device__ __forceinline__ f2pair sigma_x(float sh, float sl, f2pair x) {
-  if constexpr (FIRST) return df_mul_f(f2pair{sh, sl}, x.h);
-  else return df_mul(f2pair{sh, sl}, x);
-}
-template <int R, bool FIRST>
-__device__ __forceinline__ f2pair x_at(const float* x0, const float* delta, int i) {
-  return f2pair{x0[i], FIRST ? 0.f : delta[i * R]};
-}
-
-// rows 1 .. TT-2; returns E_0 and E_{TT-2} for the edge rows
-template <int R, int TT, bool FULL, bool FIRST, bool SM, int RS>
-__device__ __forceinline__ void residual_interior(float (&g)[TT], const float (&x0)[TT], const float* delta,
-                                                  const float* rsb, int nrows, f2pair& E0, f2pair& Elast) {
-  float sh, sl, ah = 0.f, al = 0.f;
-  if (FULL || 0 < nrows) cld4<SM>(rsb, sh, sl, ah, al);   // kS0, kS1, kA0, kA1 of row 0
-  f2pair xi = f2pair{x0[1], FIRST ? 0.f : delta[R]};
-  f2pair Ep = df_mul(f2pair{ah, al}, x_diff<FIRST>(xi, f2pair{x0[0], FIRST ? 0.f : delta[0]}));
-  E0 = Ep;
+// A5 of the first solve, as pairs: x = y + phiL xL + phiR xR with phi = PH + PL
+// and the separator values xL, xR pairs; the two products are exact up to
+// their cross terms and the three-term sum is carried exactly, so x = (xh, xl)
+// is the binary32 local solution plus the correction to ~2^-48.  The loads of
+// F for the residual are issued as each row pair frees its registers.
+template <int TT, bool SM>
+__device__ __forceinline__ void first_correction(float2 (&g)[TT / 2], float2 (&xh)[TT / 2], float* xlp, const float* cb,
+                                                 f2pair xL, f2pair xR, const Rows<const float>& f, float& maxx) {
+  constexpr int H = TT / 2;
+  const float2 xLh = f2dup(xL.h), xLl = f2dup(xL.l), xRh = f2dup(xR.h), xRl = f2dup(xR.l);
+  const float2 nxLh = f2dup(-xL.h), nxRh = f2dup(-xR.h);
 #pragma unroll
-  for (int i = 1; i < TT - 1; i++) {
-    sh = sl = ah = al = 0.f;
-    if (FULL || i < nrows) cld4<SM>(rsb + i * RS, sh, sl, ah, al);
-    const f2pair xn = f2pair{x0[i + 1], FIRST ? 0.f : delta[(i + 1) * R]};
-    const f2pair E = df_mul(f2pair{ah, al}, x_diff<FIRST>(xn, xi));
-    g[i] = residual_row(g[i], Ep, E, sigma_x<FIRST>(sh, sl, xi));
+  for (int j = 0; j < H; j++) {
+    const float4 ph = tld4<SM>(cb + j * kRefTP + kRT_PLH);   // PLH pair, PRH pair
+    const float4 pl = tld4<SM>(cb + j * kRefTP + kRT_PLL);   // PLL pair, PRL pair
+    // products and their exact errors (the negated products give the errors'
+    // addends without a negation)
+    const float2 pL = f2mul(lo2(ph), xLh);
+    float2 eL = f2fma(lo2(ph), xLh, f2mul(lo2(ph), nxLh));
+    eL = f2fma(lo2(ph), xLl, eL);
+    eL = f2fma(lo2(pl), xLh, eL);
+    const float2 pR = f2mul(hi2(ph), xRh);
+    float2 eR = f2fma(hi2(ph), xRh, f2mul(hi2(ph), nxRh));
+    eR = f2fma(hi2(ph), xRl, eR);
+    eR = f2fma(hi2(pl), xRh, eR);
+    const df2 s1 = two_sum2(pL, pR);
+    const df2 s2 = two_sum2(s1.h, g[j]);
+    xh[j] = s2.h;
+    stxl(xlp, j, f2add(f2add(eL, eR), f2add(s1.l, s2.l)));
+    maxx = fmaxf(maxx, fmaxf(fabsf(s2.h.x), fabsf(s2.h.y)));
+    g[j] = load_pair<TT>(f, j);
+  }
+}
+
+// one residual row pair: r = F - S + Ep - E, with the large fluxes Ep, E
+// cancelling exactly in the first TwoSum
+__device__ __forceinline__ float2 residual_pair(float2 F, df2 Ep, df2 E, df2 S) {
+  const df2 w = two_diff2(Ep.h, E.h);
+  const df2 u = two_sum2(F, w.h);
+  const df2 v = two_diff2(u.h, S.h);
+  const float2 small = f2add(f2sub(f2sub(Ep.l, E.l), S.l), f2add(f2add(w.l, u.l), v.l));
+  return f2add(v.h, small);
+}
+
+// Residual, first part: the row pairs j = 1 .. H-2 (rows 1 .. H-2 and
+// H+1 .. t-2), which need no value from outside the block.  Returns the flux
+// pairs E0 = {E_0, E_H} and Elast = {E_{H-2}, E_{t-2}} for the second part.
+// g holds F on entry and r on exit.
+template <int TT, bool SM>
+__device__ __forceinline__ void residual_interior(float2 (&g)[TT / 2], const float2 (&xh)[TT / 2], const float* xlp,
+                                                  const float* cb, df2& E0, df2& Elast) {
+  constexpr int H = TT / 2;
+  df2 X{xh[0], ldxl(xlp, 0)};
+  df2 Ep{};
+#pragma unroll
+  for (int j = 0; j < H - 1; j++) {
+    const df2 Xn{xh[j + 1], ldxl(xlp, j + 1)};
+    const float4 av = tld4<SM>(cb + j * kRefTP + kRT_A0);   // A0 pair, A1 pair
+    const df2 E = df2_mul(df2{lo2(av), hi2(av)}, df2_diff(Xn, X));
+    if (j == 0) {
+      E0 = E;
+    } else {
+      const float4 sv = tld4<SM>(cb + j * kRefTP + kRT_S0);   // S0 pair, S1 pair
+      const df2 S = df2_mul(df2{lo2(sv), hi2(sv)}, X);
+      g[j] = residual_pair(g[j], Ep, E, S);
+    }
     Ep = E;
-    xi = xn;
+    X = Xn;
   }
   Elast = Ep;
 }
 
-// rows 0 and TT-1, with x at the rows just outside the block (xm, xp) and
-// a_{row0-1} (aprev)
-template <int R, int TT, bool FULL, bool FIRST, bool SM, int RS>
-__device__ __forceinline__ void residual_edges(float (&g)[TT], const float (&x0)[TT], const float* delta,
-                                               const float* rsb, int nrows, f2pair aprev, f2pair xm, f2pair xp,
-                                               f2pair E0, f2pair Elast) {
-  float sh = 0.f, sl = 0.f, ah = 0.f, al = 0.f;
-  const f2pair x_first = f2pair{x0[0], FIRST ? 0.f : delta[0]};
-  if (FULL || 0 < nrows) cld4<SM>(rsb, sh, sl, ah, al);
-  const f2pair Em1 = df_mul(aprev, x_diff<FIRST>(x_first, xm));
-  g[0] = residual_row(g[0], Em1, E0, sigma_x<FIRST>(sh, sl, x_first));
-  sh = sl = ah = al = 0.f;
-  if (FULL || TT - 1 < nrows) cld4<SM>(rsb + (TT - 1) * RS, sh, sl, ah, al);
-  const f2pair x_last = f2pair{x0[TT - 1], FIRST ? 0.f : delta[(TT - 1) * R]};
-  const f2pair E = df_mul(f2pair{ah, al}, x_diff<FIRST>(xp, x_last));
-  g[TT - 1] = residual_row(g[TT - 1], Elast, E, sigma_x<FIRST>(sh, sl, x_last));
-}
-
-// A5 of a solve, in two parts.  The back substitution of the block's local
-// sweep does not depend on the separator values, so it runs while the cluster
-// barrier of A4 completes; y replaces g.
-template <bool SM>
-__device__ __forceinline__ void cld2(const float* p, float& x, float& y) {
-  float2 v;
-  if constexpr (SM) v = *reinterpret_cast<const float2*>(p);
-  else v = __ldg(reinterpret_cast<const float2*>(p));
-  x = v.x;
-  y = v.y;
-}
-template <int TT, bool FULL, bool SM>
-__device__ __forceinline__ void backward_y(float (&g)[TT], const float* cf, int nrows) {
-  float y = 0.f;
-#pragma unroll
-  for (int i = TT - 1; i >= 0; i--) {
-    if (FULL || i < nrows) {
-      float cc, invd;
-      cld2<SM>(cf + i * kNCOEF + kC, cc, invd);
-      y = fmaf(-cc, y, g[i]) * invd;
-      g[i] = y;
-    }
+// Residual, second part: the row pairs 0 and H-1, with x at the rows just
+// outside the block (xm before it, xp after it)
+template <int TT, bool SM>
+__device__ __forceinline__ void residual_edges(float2 (&g)[TT / 2], const float2 (&xh)[TT / 2], const float* xlp,
+                                               const float* cb, f2pair xm, f2pair xp, df2 E0, df2 Elast) {
+  constexpr int H = TT / 2;
+  const float2 xl0 = ldxl(xlp, 0);
+  {   // pair H-1: {E_{H-1}, E_{t-1}} needs x_H (second half's first row) and x_t (outside)
+    const df2 X{xh[H - 1], ldxl(xlp, H - 1)};
+    const df2 Xn{make_float2(xh[0].y, xp.h), make_float2(xl0.y, xp.l)};
+    const float4 av = tld4<SM>(cb + (H - 1) * kRefTP + kRT_A0);
+    const df2 E = df2_mul(df2{lo2(av), hi2(av)}, df2_diff(Xn, X));
+    const float4 sv = tld4<SM>(cb + (H - 1) * kRefTP + kRT_S0);
+    const df2 S = df2_mul(df2{lo2(sv), hi2(sv)}, X);
+    g[H - 1] = residual_pair(g[H - 1], Elast, E, S);
+    Elast = E;   // now {E_{H-1}, E_{t-1}}
   }
-}
-// Then the correction with the separator values, d = y + phiL xL + phiR xR,
-// and the update of the iterate x = x0 + delta: x0 (registers) is the first
-// solve's result, delta (shared memory, stride R) accumulates the corrections.
-//   FIRST (the first solve): x0 = d, g = 0.
-//   otherwise: d is added to delta with Knuth's TwoSum; its exact rounding
-//   error replaces g[i], so that the output can include the last one.
-// TRACK: maxd = max |d| over the block (for the convergence test).
-template <int R, int TT, bool FULL, bool SM, bool FIRST, bool TRACK>
-__device__ __forceinline__ void backward_d(float (&g)[TT], const float* cf, int nrows, float xL, float xR,
-                                           float (&x0)[TT], float* delta, float& maxd) {
-#pragma unroll
-  for (int i = 0; i < TT; i++) {
-    if (FULL || i < nrows) {
-      float phl, phr;
-      cld2<SM>(cf + i * kNCOEF + kPHIL, phl, phr);
-      const float d = fmaf(phr, xR, fmaf(phl, xL, g[i]));
-      if (FIRST) {
-        x0[i] = d;
-        g[i] = 0.f;
-      } else {
-        const f2pair sd = two_sum_f(delta[i * R], d);
-        delta[i * R] = sd.h;
-        g[i] = sd.l;
-      }
-      if (TRACK) maxd = fmaxf(maxd, fabsf(d));
-    }
+  {   // pair 0: Ep = {E_{-1}, E_{H-1}}, E = E0
+    const float2 ap = tld2<SM>(cb + kRefTail(TT));   // a of the row before the block
+    const f2pair Em1 = df_mul(f2pair{ap.x, ap.y}, df_diff(f2pair{xh[0].x, xl0.x}, xm));
+    const df2 Ep{make_float2(Em1.h, Elast.h.x), make_float2(Em1.l, Elast.l.x)};
+    const float4 sv = tld4<SM>(cb + kRT_S0);
+    const df2 S = df2_mul(df2{lo2(sv), hi2(sv)}, df2{xh[0], xl0});
+    g[0] = residual_pair(g[0], Ep, E0, S);
   }
 }
 
-template <int R, int TT, bool FULL, bool SM>
-__device__ __forceinline__ void backward_d_any(bool first, bool track, float (&g)[TT], const float* cf, int nrows,
-                                               float xL, float xR, float (&x0)[TT], float* delta, float& maxd) {
-  if (first) backward_d<R, TT, FULL, SM, true, true>(g, cf, nrows, xL, xR, x0, delta, maxd);
-  else if (track) backward_d<R, TT, FULL, SM, false, true>(g, cf, nrows, xL, xR, x0, delta, maxd);
-  else backward_d<R, TT, FULL, SM, false, false>(g, cf, nrows, xL, xR, x0, delta, maxd);
+// A5 of a correction solve: d = y + PH_L xL + PH_R xR (binary32), added to x
+// with an exact TwoSum (its error joins xl).  maxd = max |d| (for the tests).
+// With NEXT, F is reloaded into g for the next residual.
+template <int TT, bool SM, bool NEXT>
+__device__ __forceinline__ void correction_update(float2 (&g)[TT / 2], float2 (&xh)[TT / 2], float* xlp, const float* cb,
+                                                  float xL, float xR, float& maxd, const Rows<const float>& f) {
+  constexpr int H = TT / 2;
+  const float2 xL2 = f2dup(xL), xR2 = f2dup(xR);
+#pragma unroll
+  for (int j = 0; j < H; j++) {
+    const float4 ph = tld4<SM>(cb + j * kRefTP + kRT_PLH);
+    const float2 d = f2fma(hi2(ph), xR2, f2fma(lo2(ph), xL2, g[j]));
+    maxd = fmaxf(maxd, fmaxf(fabsf(d.x), fabsf(d.y)));
+    const df2 s = two_sum2(xh[j], d);
+    xh[j] = s.h;
+    stxl(xlp, j, f2add(ldxl(xlp, j), s.l));
+    g[j] = NEXT ? load_pair<TT>(f, j) : make_float2(0.f, 0.f);
+  }
 }
 
-// floats per block of the staged solve coefficients (16 bytes of padding)
-template <int TT>
-constexpr int kCfStride = TT * kNCOEF + 4;
+// Output: X = xh + xl (+ d of a last correction not yet added, FUSED) rounded
+// once to binary64; then the next item's F into g, row pair by row pair.
+template <int TT, bool SM, bool FUSED>
+__device__ __forceinline__ void output(float2 (&g)[TT / 2], const float2 (&xh)[TT / 2], const float* xlp, const float* cb,
+                                       float xL, float xR, const Rows<double>& x, const Rows<const float>& fn) {
+  constexpr int H = TT / 2;
+  const float2 xL2 = f2dup(xL), xR2 = f2dup(xR);
+#pragma unroll
+  for (int j = 0; j < H; j++) {
+    float2 hi = xh[j], lo = ldxl(xlp, j);
+    if (FUSED) {
+      const float4 ph = tld4<SM>(cb + j * kRefTP + kRT_PLH);
+      const float2 d = f2fma(hi2(ph), xR2, f2fma(lo2(ph), xL2, g[j]));
+      const df2 s = two_sum2(hi, d);
+      hi = s.h;
+      lo = f2add(lo, s.l);
+    }
+    st_stream_if(x.at(j), pair_to_f64(hi.x, lo.x), j < x.rows);
+    st_stream_if(x.at(j + H), pair_to_f64(hi.y, lo.y), j + H < x.rows);
+    g[j] = load_pair<TT>(fn, j);
+  }
+}
 
 // Shared-memory layout of the refined kernel (byte offsets; the same function
 // sizes the launch on the host).
 struct RefOffsets {
-  size_t delta, edge, red, cvg, coef, res, pad, iface, bytes;
+  size_t tab, xl, edge, red, cvg, iface, bytes;
 };
 __host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, bool sm_coef) {
   const size_t MM = (size_t)(NT / R);
   RefOffsets o{};
   size_t p = 0;
-  o.delta = p; p += round16(4 * MM * (TT + 1) * R);
+  o.tab = p; if (sm_coef) p += round16(4 * MM * (size_t)kRefTabStride(TT));
+  o.xl = p; p += round16(4 * (size_t)NT * (TT + 2));
   o.edge = p; p += round16(4 * 4 * MM * R);
-  o.red = p; p += round16(4 * 2 * MM * R);
+  o.red = p; p += round16(4 * 2 * (size_t)(NT / 32) * R);
   o.cvg = p; p += round16(4 * 5 * (size_t)R);
-  o.coef = p; if (sm_coef) p += round16(4 * MM * (TT * kNCOEF + 4));
-  o.res = p; if (sm_coef) p += round16(16 * MM * (TT + 1));
-  o.pad = p; if (sm_coef) p += round16(4 * (size_t)(TT + 1) * R);   // delta words of threads past the blocks
   o.iface = p; p += iface_offsets(R, (int)MM, true).bytes;
   o.bytes = p;
   return o;
@@ -326,69 +430,55 @@ __host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, b
 
 template <int R, int TT, int NT, int MINB, bool SM>
 __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
+  constexpr int H = TT / 2;
+  constexpr int MM = NT / R;                               // most blocks a CTA can own
+  constexpr int STR = kRefTabStride(TT);
+  constexpr int XLS = TT + 2;                              // floats per thread of xl (conflict-free float2 rows)
+  constexpr RefOffsets O = refine_offsets(R, TT, NT, SM);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float ratio_s;
-  constexpr int MM = NT / R;                               // most blocks a CTA can own
-  constexpr RefOffsets O = refine_offsets(R, TT, NT, SM);
-  const int m = L.m;
-  const int rows_cta = m * TT;
-  // Every array at a compile-time offset of the shared window.  Per-block
-  // arrays carry one padding row (sxl, sres) or 16 bytes (scf) per block: the
-  // 32 / R blocks a warp covers then fall in different banks.
-  float* const sxl = reinterpret_cast<float*>(smem_raw + O.delta);   // [MM][TT+1][R] corrections delta
+  float* const stab = reinterpret_cast<float*>(smem_raw + O.tab);    // [MM][STR] coefficient table
+  float* const sxl = reinterpret_cast<float*>(smem_raw + O.xl);      // [NT][XLS] low words of x
   float* const eFh = reinterpret_cast<float*>(smem_raw + O.edge);    // [4][MM][R] block edge values of x
   float* const eFl = eFh + MM * R;
   float* const eLh = eFl + MM * R;
   float* const eLl = eLh + MM * R;
-  float* const redD = reinterpret_cast<float*>(smem_raw + O.red);    // [2][warps][R] per-warp maxima
+  float* const red = reinterpret_cast<float*>(smem_raw + O.red);     // [2][warps][R] per-warp maxima
   float* const cvg = reinterpret_cast<float*>(smem_raw + O.cvg);     // [2][2][R] per-CTA maxima, read remotely
   float* const cvg_scratch = cvg + 4 * R;                            // [R]
-  // SM: the CTA's coefficient rows, reloaded when the series changes
-  float* const scf = reinterpret_cast<float*>(smem_raw + O.coef);    // [MM][TT*8+4]
-  float* const sres = reinterpret_cast<float*>(smem_raw + O.res);    // [MM][TT+1][4]
-  const IfaceDF<R, MM> f{smem_raw + O.iface};
+  const IfaceDF<R, MM, true> f{smem_raw + O.iface};
   const unsigned c = cluster_rank();
   const int tid = threadIdx.x;
   const int r = tid % R;
   const int bl = tid / R;
+  const int m = L.m;
   const int cluster_id = blockIdx.x / L.C;
   const int nclusters = gridDim.x / L.C;
+  float* const xlp = sxl + tid * XLS;
   // Threads past the CTA's blocks (bl >= m) only round the CTA up to whole
-  // warps.  With staged coefficients they run the same full-block code on block
-  // 0's coefficients and a scratch delta block, so that no per-row guard is
-  // compiled in; every result they produce is discarded.
-  const bool pad_thread = bl >= m;
-  float* xlt = (SM && pad_thread) ? reinterpret_cast<float*>(smem_raw + O.pad) + r
-                                  : sxl + (size_t)bl * (TT + 1) * R + r;   // this thread's delta words
+  // warps; they run the same code on zero coefficients and zero data.
 
+  float2 g[H], xh[H];
   int cur_series = -1;
   int parity = 0;
-
   bool preloaded = false;   // g already holds this item's F (loaded during the previous output)
   for (int it = cluster_id; it < L.nitems; it += nclusters) {
     // fields of the current item, read where they are used (kernel parameter
     // or work list; no address of the parameter is taken)
-#define ITEM(f) (L.single ? L.one.f : L.items[it].f)
+#define ITEM(fld) (L.single ? L.one.fld : L.items[it].fld)
     const int tile = L.single ? it : L.items[it].tile;
-    if (ITEM(series) != cur_series) {   // new series: ratios and prefix products
+    const int M = ITEM(M);
+    if (ITEM(series) != cur_series) {   // new series: ratios, products, coefficient rows
       __syncthreads();
-      iface_df_setup(f, ITEM(rR), ITEM(rL), ITEM(M), m, L.C, c);
-      if constexpr (SM) {   // rows past n are staged as zeros
-        const int64_t cta_row0 = (int64_t)c * rows_cta;
-        for (int k = tid; k < rows_cta * kNCOEF / 4; k += blockDim.x) {
-          const int rr = (k * 4) / kNCOEF;   // row within the CTA
-          const int64_t row = cta_row0 + rr;
-          float x = 0.f, y = 0.f, z = 0.f, w = 0.f;
-          if (row < ITEM(n)) ldg4(ITEM(coef) + cta_row0 * kNCOEF + (int64_t)k * 4, x, y, z, w);
-          float* d = scf + (size_t)(rr / TT) * kCfStride<TT> + (size_t)(rr % TT) * kNCOEF + (k * 4) % kNCOEF;
-          d[0] = x; d[1] = y; d[2] = z; d[3] = w;
-        }
-        for (int k = tid; k < m * (TT + 1); k += blockDim.x) {   // block j: rows j*TT-1 .. j*TT+TT-1
-          const int64_t row = cta_row0 + (int64_t)(k / (TT + 1)) * TT + (k % (TT + 1)) - 1;
-          float x = 0.f, y = 0.f, z = 0.f, w = 0.f;
-          if (row >= 0 && row < ITEM(n)) ldg4(ITEM(res) + row * kNRES, x, y, z, w);   // kS0, kS1, kA0, kA1
-          float* d = sres + (size_t)k * 4;
-          d[0] = x; d[1] = y; d[2] = z; d[3] = w;
+      iface_df_setup(f, ITEM(rR), ITEM(rL), M, m, L.C, c);
+      if constexpr (SM) {   // this CTA's blocks of the table; blocks past M as zeros
+        const float4* src = reinterpret_cast<const float4*>(ITEM(tab) + (size_t)c * m * STR);
+        float4* dst = reinterpret_cast<float4*>(stab);
+        for (int k = tid; k < MM * STR / 4; k += blockDim.x) {
+          const int blk = (k * 4) / STR;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (blk < m && (int)c * m + blk < M) v = __ldg(src + k);
+          dst[k] = v;
         }
       }
       __syncthreads();
@@ -396,197 +486,152 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
     }
     const int n = ITEM(n);
     const int b = (int)c * m + bl;
-    const bool blk_ok = (bl < m) && (b < ITEM(M));
+    const bool blk_ok = (bl < m) && (b < M);
     const int64_t row0 = (int64_t)b * TT;
     const int nrows = blk_ok ? (int)((n - row0) < TT ? (n - row0) : TT) : 0;
     const int64_t col = (int64_t)tile * R + r;
     const bool col_ok = col < ITEM(N);
     const bool active = nrows > 0 && col_ok;   // this thread's rows and column exist
-    const bool full_rows = nrows == TT;
-    // Arithmetic over all TT rows: with staged coefficients the rows past n
-    // are zeros (F, x and every coefficient), so only F and X need guards.
-    const bool full = full_rows;   // (staged coefficients: the full-block code runs always)
-    const int blc = (SM && pad_thread) ? 0 : bl;
-    const float* Fp = ITEM(F) + row0 * ITEM(ldF) + col;
-    // this block's coefficient rows (rsb[-RS] is the row before the block)
-    const float* cfb = SM ? scf + (size_t)blc * kCfStride<TT> : ITEM(coef) + row0 * kNCOEF;
-    const float* rsb = SM ? sres + (size_t)(blc * (TT + 1) + 1) * 4 : ITEM(res) + row0 * kNRES;
-    constexpr int RS = SM ? 4 : kNRES;   // stride of the residual coefficient rows
-    const bool adaptive = ITEM(steps) <= 0;
-    const int cap = adaptive ? 4 : ITEM(steps);
+    const float* cb = SM ? stab + (size_t)bl * STR : ITEM(tab) + (size_t)(blk_ok ? b : M) * STR;
+    // this thread's rows of F (none for padding threads and missing columns)
+    const Rows<const float> fr{ITEM(F) + row0 * ITEM(ldF) + col, (int)ITEM(ldF), active ? nrows : 0};
+    const int steps_cfg = ITEM(steps);
+    const bool adaptive = steps_cfg == -1;
+    const bool calib = steps_cfg == kRefineCalib;
+    const bool track = adaptive || calib;
+    const int cap = adaptive ? kRefineCap : (calib ? kRefineCalibSteps : steps_cfg);
 
-    float xh[TT], g[TT];
-#pragma unroll
-    for (int i = 0; i < TT; i++) {
-      xh[i] = 0.f;
-      if (SM || bl < m) xlt[i * R] = 0.f;
-    }
-    if (!preloaded) {
-      if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
-      else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
-    }
-    bool have_f = false;   // g holds F for the next residual (loaded right after the last solve)
+    if (!preloaded) load_rhs<TT>(g, fr);
 
-    float ratio_prev = 1.f;
-    float maxx = 0.f;   // max |x0| of this thread's rows (the first solve)
-    int cpar = 0;
-    for (int step = 0;; step++) {
-      if (step > 0) {
-        // ---- residual r = F - A x of the current iterate ------------------------
-        if (bl < m) {
-          eFh[bl * R + r] = xh[0]; eFl[bl * R + r] = xlt[0];
-          eLh[bl * R + r] = xh[TT - 1]; eLl[bl * R + r] = xlt[(TT - 1) * R];
-        }
-        // Adaptive refinement makes at least two corrections; from the third
-        // step on it first tests the last one (estimated error
-        // ratio_k^2 / ratio_{k-1}), which needs every CTA's maxima.  Otherwise
-        // the interior of the residual overlaps the edge-value barrier.
-        const bool test = adaptive && step >= 3;
-        if (test) {
-          cluster_barrier();
-          if (step == 3) ratio_prev = cluster_ratio<R>(cvg + cpar * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
-          const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
-          const bool stop = ratio * ratio <= kRefineTol * ratio_prev;
-          ratio_prev = ratio;
-          if (stop) {
-            if (tid == 0 && c == 0) atomicMax(&g_tdm_corrections_max, step - 1);
-            break;
-          }
-        } else {
-          cluster_arrive();
-        }
-        f2pair E0{0.f, 0.f}, Elast{0.f, 0.f};
-        if (bl < m) {
-          if (!have_f) {
-            if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
-            else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
-          }
-          have_f = false;
-          if (nrows > 0) {
-            if (step == 1) {   // delta is still zero
-              if (SM || full) residual_interior<R, TT, true, true, SM, RS>(g, xh, xlt, rsb, nrows, E0, Elast);
-              else residual_interior<R, TT, SM, true, SM, RS>(g, xh, xlt, rsb, nrows, E0, Elast);
-            } else {
-              if (SM || full) residual_interior<R, TT, true, false, SM, RS>(g, xh, xlt, rsb, nrows, E0, Elast);
-              else residual_interior<R, TT, SM, false, SM, RS>(g, xh, xlt, rsb, nrows, E0, Elast);
-            }
-          }
-        }
-        if (!test) cluster_wait();
-        if (bl < m) {
-          f2pair xm{0.f, 0.f}, xp{0.f, 0.f};   // x at rows row0-1 and row0+TT
-          if (bl > 0) {
-            xm = f2pair{eLh[(bl - 1) * R + r], eLl[(bl - 1) * R + r]};
-          } else if (c > 0) {
-            xm = f2pair{ld_cluster_f32(eLh + (m - 1) * R + r, c - 1), ld_cluster_f32(eLl + (m - 1) * R + r, c - 1)};
-          }
-          if (bl < m - 1) {
-            xp = f2pair{eFh[(bl + 1) * R + r], eFl[(bl + 1) * R + r]};
-          } else if ((int)c < L.C - 1) {
-            xp = f2pair{ld_cluster_f32(eFh + r, c + 1), ld_cluster_f32(eFl + r, c + 1)};
-          }
-          if (nrows > 0) {
-            // a_{row0-1}, for the flux into the first row
-            f2pair aprev{0.f, 0.f};
-            if (row0 > 0) aprev = f2pair{rsb[-RS + kA0], rsb[-RS + kA1]};
-            if (step == 1) {
-              if (SM || full) residual_edges<R, TT, true, true, SM, RS>(g, xh, xlt, rsb, nrows, aprev, xm, xp, E0, Elast);
-              else residual_edges<R, TT, SM, true, SM, RS>(g, xh, xlt, rsb, nrows, aprev, xm, xp, E0, Elast);
-            } else {
-              if (SM || full) residual_edges<R, TT, true, false, SM, RS>(g, xh, xlt, rsb, nrows, aprev, xm, xp, E0, Elast);
-              else residual_edges<R, TT, SM, false, SM, RS>(g, xh, xlt, rsb, nrows, aprev, xm, xp, E0, Elast);
-            }
-          }
-        }
-      }
-      // ---- binary32 dichotomy solve of g (A2-A5) ---------------------------------
-      float bR = 0.f, bL = 0.f;
-      if (SM || full) forward_pass_g<TT, true, SM>(g, cfb, nrows, bR, bL);
-      else forward_pass_g<TT, SM, SM>(g, cfb, nrows, bR, bL);
-      if (bl < m) {
-        f.beR()[bl * f.kRP + r] = bR;
-        f.beL()[bl * f.kRP + r] = bL;
-      }
+    // ---- first solve (A2-A5): x = (xh, xl) ------------------------------------
+    float maxx = 0.f;
+    {
+      float bR, bL;
+      forward_pass<TT, SM>(g, cb, bR, bL);
+      f.beR()[bl * f.kRP + r] = bR;
+      f.beL()[bl * f.kRP + r] = bL;
       __syncthreads();
-      iface_df_scan<R>(f, m, parity);
+      iface_df_scan<R, MM, true, true>(f, m, parity);
       cluster_arrive();   // the back substitution overlaps the exchange of the CTA totals
-      if (SM || full) backward_y<TT, true, SM>(g, cfb, nrows);
-      else backward_y<TT, SM, SM>(g, cfb, nrows);
+      backward_y<TT, SM>(g, cb);
       cluster_wait();
-      iface_df_fold<R>(f, L.C, c, parity);
+      iface_df_fold<R, MM, true, true>(f, L.C, c, parity);
+      __syncthreads();
+      parity ^= 1;
+      f2pair xL{0.f, 0.f}, xR{0.f, 0.f};
+      if (blk_ok) {
+        if (b >= 1) xL = iface_df_sep_pair<R, MM, true, true>(f, bl, r);
+        if (b + 1 <= M - 1) xR = iface_df_sep_pair<R, MM, true, true>(f, bl + 1, r);
+      }
+      first_correction<TT, SM>(g, xh, xlp, cb, xL, xR, fr, maxx);
+    }
+    if (!col_ok) maxx = 0.f;
+
+    // ---- corrections: r = F - A x, d = solve(r), x += d ----------------------
+    const int64_t ldX = ITEM(ldX);
+    const Rows<double> xr{ITEM(X) + row0 * ldX + col, (int)ldX, active ? nrows : 0};
+    // the next item's F, loaded during the output
+    const int it2 = it + nclusters;
+    preloaded = it2 < L.nitems;
+    Rows<const float> fn{ITEM(F), 0, 0};
+    if (preloaded) {
+#define ITEM2(fld) (L.single ? L.one.fld : L.items[it2].fld)
+      const int tile_n = L.single ? it2 : L.items[it2].tile;
+      const int64_t col_n = (int64_t)tile_n * R + r;
+      const int n_n = ITEM2(n);
+      if ((bl < m) && (b < ITEM2(M)) && col_n < ITEM2(N)) {
+        fn.rows = (int)((n_n - row0) < TT ? (n_n - row0) : TT);
+        fn.ld32 = (int)ITEM2(ldF);
+        fn.base = ITEM2(F) + row0 * ITEM2(ldF) + col_n;
+      }
+#undef ITEM2
+    }
+    float ratio_prev = 1.f;
+    int done = 0;
+    bool fused_out = false;
+    while (true) {
+      if (done == cap) break;
+      // edge values of x for the neighbours' residuals
+      eFh[bl * R + r] = xh[0].x;
+      eFl[bl * R + r] = ldxl(xlp, 0).x;
+      eLh[bl * R + r] = xh[H - 1].y;
+      eLl[bl * R + r] = ldxl(xlp, H - 1).y;
+      // Tests read every CTA's maxima of the last correction: a full cluster
+      // barrier, which also publishes the edge values.  Otherwise the interior
+      // of the residual overlaps the edge-value barrier.
+      const bool test = track && done >= 1;
+      if (test) {
+        cluster_barrier();
+        const float ratio = cluster_ratio<R>(cvg + (done & 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
+        if (calib && tid == 0 && c == 0) atomicMax(&g_tdm_calib[done - 1], __float_as_uint(ratio));
+        if (adaptive) {
+          const bool stop = done == 1 ? ratio * ITEM(contraction) <= kRefineTol1
+                                      : ratio * ratio <= kRefineTol * ratio_prev;
+          ratio_prev = ratio;
+          if (stop) break;
+        }
+      } else {
+        cluster_arrive();
+      }
+      df2 E0, Elast;
+      residual_interior<TT, SM>(g, xh, xlp, cb, E0, Elast);
+      if (!test) cluster_wait();
+      f2pair xm{0.f, 0.f}, xp{0.f, 0.f};   // x at rows row0-1 and row0+TT
+      if (bl > 0) {
+        xm = f2pair{eLh[(bl - 1) * R + r], eLl[(bl - 1) * R + r]};
+      } else if (c > 0) {
+        xm = f2pair{ld_cluster_f32(eLh + (m - 1) * R + r, c - 1), ld_cluster_f32(eLl + (m - 1) * R + r, c - 1)};
+      }
+      if (bl < m - 1) {
+        xp = f2pair{eFh[(bl + 1) * R + r], eFl[(bl + 1) * R + r]};
+      } else if ((int)c < L.C - 1) {
+        xp = f2pair{ld_cluster_f32(eFh + r, c + 1), ld_cluster_f32(eFl + r, c + 1)};
+      }
+      residual_edges<TT, SM>(g, xh, xlp, cb, xm, xp, E0, Elast);
+
+      // ---- correction solve, all binary32 --------------------------------------
+      float bR, bL;
+      forward_pass<TT, SM>(g, cb, bR, bL);
+      f.beR()[bl * f.kRP + r] = bR;
+      f.beL()[bl * f.kRP + r] = bL;
+      __syncthreads();
+      iface_df_scan<R, MM, true, false>(f, m, parity);
+      cluster_arrive();
+      backward_y<TT, SM>(g, cb);
+      cluster_wait();
+      iface_df_fold<R, MM, true, false>(f, L.C, c, parity);
       __syncthreads();
       parity ^= 1;
       float xL = 0.f, xR = 0.f;
       if (blk_ok) {
-        if (b >= 1) xL = iface_df_sep<R>(f, bl, r);
-        if (b + 1 <= ITEM(M) - 1) xR = iface_df_sep<R>(f, bl + 1, r);
+        if (b >= 1) xL = iface_df_sep_pair<R, MM, true, false>(f, bl, r).h;
+        if (b + 1 <= M - 1) xR = iface_df_sep_pair<R, MM, true, false>(f, bl + 1, r).h;
       }
-      float maxd = 0.f;
-      const bool first = step == 0;
-      if (SM || full) backward_d_any<R, TT, true, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
-      else backward_d_any<R, TT, SM, SM>(first, adaptive, g, cfb, nrows, xL, xR, xh, xlt, maxd);
-      if (!col_ok) maxd = 0.f;   // padding columns of a ragged tile do not vote
-      if (first) {
-        maxx = maxd;
-      } else if (adaptive) {   // per-CTA, per-column maxima of |d| and |x0| for the test
-        cta_maxima<R>(maxd, maxx, redD, cvg + cpar * 2 * R, tid);
-        cpar ^= 1;
-      }
-      // when another correction is certain, the last rounding errors in g are
-      // not needed: reload F now, so that the loads overlap the bookkeeping
-      // and the edge-value exchange
-      if (step < cap && (!adaptive || step < 2) && bl < m) {
-        if (full_rows) load_rhs<TT, true>(g, Fp, ITEM(ldF), active, nrows);
-        else load_rhs<TT, false>(g, Fp, ITEM(ldF), active, nrows);
-        have_f = true;
-      }
-      if (step == cap) {
-        if (adaptive) {   // cap reached: record whether the last correction met the test
-          cluster_barrier();
-          if (step < 3) ratio_prev = step == 2 ? cluster_ratio<R>(cvg + cpar * 2 * R, L.C, tid, cvg_scratch, &ratio_s)
-                                               : 1.f;
-          const float ratio = cluster_ratio<R>(cvg + (cpar ^ 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
-          if (tid == 0 && !(ratio * ratio <= kRefineTol * ratio_prev)) atomicExch(L.err, kDevErrNotConverged);
-          if (tid == 0 && c == 0) atomicMax(&g_tdm_corrections_max, cap);
-        }
+      done++;
+      if (!track && done == cap) {   // the last correction is added in the output
+        output<TT, SM, true>(g, xh, xlp, cb, xL, xR, xr, fn);
+        fused_out = true;
         break;
       }
-    }
-    // ---- X = x0 + delta + (last rounding error, in g), rounded once to binary64 ----
-    // Each row's g is free once the row is stored: the next item's F row is
-    // loaded into it there, so that its latency overlaps the rest of the output.
-    {
-      const int it2 = it + nclusters;
-      preloaded = it2 < L.nitems;
-      const float* Fn = nullptr;
-      int64_t ldn = 0;
-      int nrows_n = 0;
-      if (preloaded) {
-#define ITEM2(f) (L.single ? L.one.f : L.items[it2].f)
-        const int tile_n = L.single ? it2 : L.items[it2].tile;
-        const int64_t col_n = (int64_t)tile_n * R + r;
-        const int n_n = ITEM2(n);
-        if ((bl < m) && (b < ITEM2(M)) && col_n < ITEM2(N)) {
-          nrows_n = (int)((n_n - row0) < TT ? (n_n - row0) : TT);
-          ldn = ITEM2(ldF);
-          Fn = ITEM2(F) + row0 * ldn + col_n;
-        }
-#undef ITEM2
-      }
-      const int64_t ldX = ITEM(ldX);
-      double* Xp = ITEM(X) + row0 * ldX + col;
-#pragma unroll
-      for (int i = 0; i < TT; i++) {
-        if (active && (full_rows || i < nrows)) {
-          const f2pair sx = two_sum_f(xh[i], xlt[i * R]);
-          st_stream(Xp, tdm_f2d(sx.h) + tdm_f2d(sx.l + g[i]));
-        }
-        Xp += ldX;
-        g[i] = i < nrows_n ? ld_stream(Fn + (int64_t)i * ldn) : 0.f;
+      float maxd = 0.f;
+      if (done < cap) correction_update<TT, SM, true>(g, xh, xlp, cb, xL, xR, maxd, fr);
+      else correction_update<TT, SM, false>(g, xh, xlp, cb, xL, xR, maxd, fr);
+      if (track) {
+        if (!col_ok) maxd = 0.f;   // padding columns of a ragged tile do not vote
+        cta_maxima<R>(maxd, maxx, red, cvg + (done & 1) * 2 * R, tid);
       }
     }
-  }
+    if (!fused_out) {
+      if (track && done == cap) {   // cap reached: record the last correction
+        cluster_barrier();
+        const float ratio = cluster_ratio<R>(cvg + (done & 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
+        if (calib && tid == 0 && c == 0) atomicMax(&g_tdm_calib[done - 1], __float_as_uint(ratio));
+        if (adaptive && tid == 0 && !(ratio * ratio <= kRefineTol * ratio_prev)) atomicExch(L.err, kDevErrNotConverged);
+      }
+      output<TT, SM, false>(g, xh, xlp, cb, 0.f, 0.f, xr, fn);
+    }
 #undef ITEM
+  }
   // no CTA may leave while a peer can still read its shared memory
   cluster_barrier();
 }
@@ -633,42 +678,48 @@ tdm_status launch_shape(const RefShape& sh, const RefLaunch& L, int nitems, cuda
   return TDM_OK;
 }
 
+struct RefCand {
+  int R, NT;
+  bool sm;
+};
+// the shapes of each block size, in the rule's order
+constexpr RefCand kCand32[] = {{8, 256, true}, {8, 512, true}, {4, 512, false}, {16, 512, true}};
+constexpr RefCand kCand16[] = {{8, 256, true}, {8, 512, true}, {4, 1024, false}};
+constexpr int kRule32 = 3, kRule16 = 3;   // candidates the rule tries (the rest only on request)
+
 }  // namespace
 
 // Tile shapes: R right-hand sides per tile, NT threads per CTA, m = NT / R
 // blocks of t rows per CTA, up to 16 CTAs per cluster.
-//   t = 16: R = 8, 512 threads, two CTAs per SM (64 registers), 1024 rows per
-//           CTA (n <= 16384); R = 4 with 512 threads (2048 rows) or 1024
-//           threads (4096 rows, n <= 65536), coefficients read through L1.
-//   t = 32: R = 8, 256 threads, two CTAs per SM (128 registers, n <= 16384);
-//           R = 8, 512 threads, one CTA per SM (n <= 32768); R = 4, 512
-//           threads, coefficients read through L1 (n <= 65536); R = 16,
-//           512 threads on request.
+//   t = 32: R = 8, 256 threads, two CTAs per SM, table in shared memory
+//           (n <= 16384); R = 8, 512 threads (n <= 32768); R = 4, 512 threads,
+//           table read through L1 (n <= 65536); R = 16, 512 threads on request.
+//   t = 16: R = 8, 256 threads (n <= 8192); R = 8, 512 threads (n <= 16384);
+//           R = 4, 1024 threads, table through L1 (n <= 65536).
 // A requested width (pref) is tried first; the rule's shapes follow.
 bool tdm_refined_shape(int M, int t, int pref, RefShape& sh) {
-  struct Cand { int R, NT; bool sm; };
-  // the requested width first (16 exists for 32-row blocks only)
-  const Cand want = {pref == 16 && t == 16 ? 0 : pref, pref == 8 && t == 32 ? 256 : 512, pref != 4};
-  const Cand c16[4] = {{8, 512, true}, {4, 512, false}, {4, 1024, false}, {4, 1024, false}};
-  const Cand c32[4] = {{8, 256, true}, {8, 512, true}, {4, 512, false}, {4, 512, false}};
-  const Cand* rule = t == 16 ? c16 : c32;
-  for (int k = pref ? -1 : 0; k < 4; k++) {
-    const Cand* cand = k < 0 ? &want : rule;
-    const int idx = k < 0 ? 0 : k;
-    const int R = cand[idx].R, NT = cand[idx].NT;
-    if (R != 4 && R != 8 && R != 16) continue;
-    const int m_max = NT / R;
+  const RefCand* cand = t == 16 ? kCand16 : kCand32;
+  const int ncand = t == 16 ? (int)(sizeof(kCand16) / sizeof(kCand16[0])) : (int)(sizeof(kCand32) / sizeof(kCand32[0]));
+  const int nrule = t == 16 ? kRule16 : kRule32;
+  auto fits = [&](const RefCand& k) -> bool {
+    const int m_max = k.NT / k.R;
     const int C = (M + m_max - 1) / m_max;
-    if (C > 16) continue;
+    if (C > 16) return false;
     const int m = (M + C - 1) / C;
-    sh.R = R; sh.NT = NT; sh.m = m; sh.C = C;
-    sh.threads = ((m * R + 31) / 32) * 32;
+    const size_t smem = refine_offsets(k.R, t, k.NT, k.sm).bytes;
+    if (smem > 227 * 1024) return false;
+    sh.R = k.R; sh.NT = k.NT; sh.m = m; sh.C = C;
+    sh.threads = ((m * k.R + 31) / 32) * 32;
     if (sh.threads < 96) sh.threads = 96;
-    sh.sm_coef = cand[idx].sm;
-    sh.smem = refine_offsets(R, t, NT, sh.sm_coef).bytes;
-    if (sh.smem > 227 * 1024) continue;
+    sh.sm_coef = k.sm;
+    sh.smem = smem;
     return true;
-  }
+  };
+  if (pref)
+    for (int k = 0; k < ncand; k++)
+      if (cand[k].R == pref && fits(cand[k])) return true;
+  for (int k = 0; k < nrule; k++)
+    if (fits(cand[k])) return true;
   return false;
 }
 
@@ -690,8 +741,8 @@ tdm_status tdm_refined_launch(const RefShape& sh, int t, const RefItem* items, c
     case 8 * 100000 + 512 * 10 + 0: return launch_shape<8, 32, 512, 1, true>(sh, L, nitems, s);
     case 4 * 100000 + 512 * 10 + 0: return launch_shape<4, 32, 512, 1, false>(sh, L, nitems, s);
     case 16 * 100000 + 512 * 10 + 0: return launch_shape<16, 32, 512, 1, true>(sh, L, nitems, s);
-    case 8 * 100000 + 512 * 10 + 1: return launch_shape<8, 16, 512, 2, true>(sh, L, nitems, s);
-    case 4 * 100000 + 512 * 10 + 1: return launch_shape<4, 16, 512, 2, false>(sh, L, nitems, s);
+    case 8 * 100000 + 256 * 10 + 1: return launch_shape<8, 16, 256, 2, true>(sh, L, nitems, s);
+    case 8 * 100000 + 512 * 10 + 1: return launch_shape<8, 16, 512, 1, true>(sh, L, nitems, s);
     case 4 * 100000 + 1024 * 10 + 1: return launch_shape<4, 16, 1024, 1, false>(sh, L, nitems, s);
   }
   return TDM_ERR_NOT_IMPLEMENTED;
@@ -702,15 +753,17 @@ RefItem tdm_refined_item(const tdm_plan_s* p, const float* F, int64_t ldF, doubl
   RefItem it;
   memset(&it, 0, sizeof(it));
   it.F = F; it.X = X; it.ldF = ldF; it.ldX = ldX;
-  it.coef = p->coef32; it.res = p->res32; it.rR = p->rR; it.rL = p->rL;
+  it.tab = p->rtab; it.rR = p->rR; it.rL = p->rL;
   it.n = (int)p->n; it.M = p->M; it.N = (int)N; it.tile = 0;
   it.series = series;
   it.steps = p->refine_steps;
+  it.contraction = p->contraction;
   return it;
 }
 
 tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX, int64_t N,
                               cudaStream_t s) {
+  if (ldF > kRefMaxLd || ldX > kRefMaxLd) return TDM_ERR_NOT_IMPLEMENTED;
   RefShape sh;
   if (!tdm_refined_shape(p->M, p->t, p->tile_rhs, sh)) return TDM_ERR_NOT_IMPLEMENTED;
   const RefItem one = tdm_refined_item(p, F, ldF, X, ldX, N, 0);
@@ -718,15 +771,16 @@ tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double
   return tdm_refined_launch(sh, p->t, nullptr, &one, ntiles, p->dev_err, s);
 }
 
-// Clears / reads the corrections counter of the current device (calibration).
-tdm_status tdm_corrections_counter(bool clear, int* value, cudaStream_t s) {
+// Clears / reads the calibration record of the current device.
+tdm_status tdm_calibration_record(bool clear, float* ratios, cudaStream_t s) {
+  unsigned v[kRefineCalibSteps] = {0, 0, 0, 0};
   if (clear) {
-    const int zero = 0;
-    TDM_CUDA_TRY(cudaMemcpyToSymbolAsync(g_tdm_corrections_max, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    TDM_CUDA_TRY(cudaMemcpyToSymbolAsync(g_tdm_calib, v, sizeof(v), 0, cudaMemcpyHostToDevice, s));
     TDM_CUDA_TRY(cudaStreamSynchronize(s));
   } else {
-    TDM_CUDA_TRY(cudaMemcpyFromSymbolAsync(value, g_tdm_corrections_max, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    TDM_CUDA_TRY(cudaMemcpyFromSymbolAsync(v, g_tdm_calib, sizeof(v), 0, cudaMemcpyDeviceToHost, s));
     TDM_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int k = 0; k < kRefineCalibSteps; k++) memcpy(&ratios[k], &v[k], sizeof(float));
   }
   return TDM_OK;
 }

@@ -1,24 +1,53 @@
-// tdm_refine.cuh -- work items of the refined persistent kernel (shared by the
-// single-series and the batched launch paths).
+// tdm_refine.cuh -- work items and the coefficient table of the refined
+// persistent kernel (shared by the single-series and the batched launch paths,
+// and by the prepare step that builds the table).
 #pragma once
 
 #include <stdint.h>
 
 #include "tdm_internal.cuh"
 
+// ---------------------------------------------------------------------------
+// Coefficient table of the refined kernel, [M + 1][kRefTabStride(t)] binary32
+// (the extra block is all zeros).  Per block:
+//  * t/2 row pairs of kRefTP floats: the kernel holds a block's rows as pairs
+//    (row j, row j + t/2), so these coefficients are stored as such pairs,
+//      GR, GL     beta weights G_{p_{b+1}}(i), G_{p_b}(i)        (eq. beta_symn)
+//      PLH, PRH   phiL, phiR rounded to binary32                  (Lemma 1)
+//      PLL, PRL   phiL - PLH, phiR - PRH rounded to binary32 (the first solve's
+//                 correction is formed with phi to ~2^-48)
+//      S0, S1     sigma_i = b_i + a_{i-1} + a_i as a binary32 pair (residual)
+//      A0, A1     a_i as a binary32 pair (residual);
+//  * the local sweep, row by row: the forward multipliers of rows 0 .. t-1
+//    (t floats, four per vector load), then the back substitution's
+//    (off-diagonal, 1 / pivot) of rows t-1, t-2, ..., 0 (2t floats, two rows
+//    per vector load, in the order the substitution walks them);
+//  * 4 floats: A0, A1 of the row before the block (a_{row0-1}), 0, 0.
+// Rows at or past n are zeros.
+// ---------------------------------------------------------------------------
+enum {
+  kRT_GR = 0, kRT_GL = 2, kRT_PLH = 4, kRT_PRH = 6, kRT_PLL = 8, kRT_PRL = 10,
+  kRT_S0 = 12, kRT_S1 = 14, kRT_A0 = 16, kRT_A1 = 18, kRefTP = 20
+};
+__host__ __device__ constexpr int kRefLF(int t) { return (t / 2) * kRefTP; }        // forward multipliers
+__host__ __device__ constexpr int kRefCI(int t) { return kRefLF(t) + t; }            // back substitution
+__host__ __device__ constexpr int kRefTail(int t) { return kRefCI(t) + 2 * t; }      // a_{row0-1}
+__host__ __device__ constexpr int kRefTabStride(int t) { return kRefTail(t) + 4; }
+
 // one tile of one series (an entry of a device-resident work list)
 struct RefItem {
   const float* F;
   double* X;
   int64_t ldF, ldX;
-  const float* coef;   // [n][8] solve coefficients (binary32)
-  const float* res;    // [n][8] residual coefficients
+  const float* tab;    // [M + 1][kRefTabStride(t)] coefficient table
+  const void* spare;   // unused (keeps the item at 96 bytes)
   const double* rR;
   const double* rL;
   int n, M, N, tile;
   int series;          // series number: ratios are set up again when it changes
-  int steps;           // refinement steps (0 = adaptive)
-  int pad0, pad1;
+  int steps;           // corrections: k >= 1 exactly k; -1 tested per tile; -2 calibration
+  float contraction;   // tested: estimated error after the first correction = its size x this
+  int pad1;
 };
 
 struct RefLaunch {
@@ -33,16 +62,26 @@ struct RefLaunch {
 // tile shape of the refined kernel for a series of M blocks of t rows
 struct RefShape {
   int R = 0, NT = 0, m = 0, C = 0, threads = 0;
-  bool sm_coef = true;   // coefficient rows staged in shared memory
+  bool sm_coef = true;   // coefficient table staged in shared memory
   size_t smem = 0;
 };
+
+// largest row stride (elements) of F and X the refined kernel addresses with
+// 32-bit row offsets
+constexpr int64_t kRefMaxLd = int64_t(1) << 26;
+
+// steps value of a calibration solve: kRefineCalibSteps corrections, with the
+// size of every correction recorded
+constexpr int kRefineCalib = -2;
+constexpr int kRefineCalibSteps = 4;
 
 // pref: requested right-hand sides per tile (0 = by the rule)
 bool tdm_refined_shape(int M, int t, int pref, RefShape& sh);
 // enqueue one launch over `nitems` items (items == nullptr: single series `one`)
 tdm_status tdm_refined_launch(const RefShape& sh, int t, const RefItem* items, const RefItem* one,
                               int nitems, int* err, cudaStream_t s);
-// the prepare-time calibration's view of the corrections per-tile-tested tiles made
-tdm_status tdm_corrections_counter(bool clear, int* value, cudaStream_t s);
+// the calibration record: max over tiles of max|d_k| / max|x| for corrections
+// k = 1 .. kRefineCalibSteps of calibration solves (cleared, or read into ratios)
+tdm_status tdm_calibration_record(bool clear, float* ratios, cudaStream_t s);
 RefItem tdm_refined_item(const tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX,
                          int64_t N, int series);
