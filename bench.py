@@ -247,7 +247,10 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if N_RHS == 8192 else WORKLOAD.replace("N=8192", f"N={N_RHS}"),
                    "n": N_ROWS, "N": N_RHS, "s": SHIFT, "precision": "fp32_refined",
-                   "output": "f64", "refine_steps": info["refine_steps"], "block_rows": info["block_rows"],
+                   "output": "f64", "refine_steps": info["refine_steps"], "contraction": info["contraction"],
+                   "refinement": "one correction per tile, checked against the plan's calibrated contraction "
+                                 "during the next tile; a failing tile is solved again with more",
+                   "block_rows": info["block_rows"],
                    "parallelism": f"rhs-sharded x{DIST['world']}" if DIST["world"] > 1 else "single GPU",
                    "l2": "no flush: F (512 MiB) and X (1 GiB) exceed L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

@@ -83,13 +83,16 @@ typedef struct {
                           k in 1..4: exactly k, no test;
                           -1: every tile of right-hand sides tests its own corrections: after
                               the first, stop if its size max|d_1| / max|x| times the plan's
-                              contraction is below 2.5e-12; after the k-th (k >= 2), stop if the
+                              contraction is below 4e-12; after the k-th (k >= 2), stop if the
                               estimated relative error max|d_k|^2 / (max|x| max|d_{k-1}|) is
                               below 1e-12; at most 4 (device_error 2 otherwise).  Requested
                               explicitly, the contraction is 1 (at least two corrections);
                           0 (automatic): -1 with the contraction measured by tdm_prepare on 64
-                              seeded right-hand sides (four corrections: twice the size of the
-                              second per unit of the first).  Plans too large to calibrate cheaply
+                              seeded right-hand sides (four corrections: the size of the second
+                              per unit of the first).  Each tile then makes its first correction,
+                              writes X and is checked during the next tile's first exchange; a
+                              tile that fails is solved again with the tests after every
+                              correction.  Plans too large to calibrate cheaply
                               (n > ~350000 uses fewer columns, n > ~2.8e6 none) keep contraction 1.
                               tdm_info reports both. */
   int flags;         /* reserved, must be 0 */

@@ -452,8 +452,7 @@ extern "C" tdm_status tdm_destroy(tdm_handle h) {
 // a property of the matrix and of the binary32 solve more than of F.  The plan
 // then tests every tile of right-hand sides after its first correction with
 // that contraction (estimated error = size of the first correction x the
-// contraction, kept twice as large as measured) and after later ones with the
-// ratio test (tdm_refine.cu).  Right-hand sides like the calibration's stop
+// contraction) and after later ones with the ratio test (tdm_refine.cu).  Right-hand sides like the calibration's stop
 // after one correction; ones whose first solve is far less accurate relative
 // to their solution (pure high modes of an ill-conditioned matrix) take more.
 // Plans too large for a cheap calibration keep contraction 1: at least two
@@ -507,7 +506,7 @@ tdm_status calibrate_refinement(tdm_plan_s* p, cudaStream_t s) {
   (void)cudaGetLastError();
   // ratios[k]: the size of correction k + 1
   if (st == TDM_OK && h_err == 0 && ratios[0] > 0.f && ratios[1] < ratios[0])
-    p->contraction = 2.f * ratios[1] / ratios[0];
+    p->contraction = ratios[1] / ratios[0];
   else if (st == TDM_OK && h_err == 0 && ratios[0] == 0.f)
     p->contraction = 0.f;   // the first solve was exact on the calibration columns
   return st;

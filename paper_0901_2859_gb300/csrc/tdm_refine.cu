@@ -67,12 +67,13 @@ using namespace tdmk;
 
 // Per-tile test (refine_steps = -1), with ratio_k = max over the tile's columns
 // of max|d_k| / max|x|: after the first correction, stop once ratio_1 times the
-// plan's contraction (measured at prepare: the error left after one correction
-// per unit of its size) is below kRefineTol1; after correction k >= 2, once
-// the estimated relative error ratio_k^2 / ratio_{k-1} (linear convergence) is
-// below kRefineTol.
+// plan's contraction (measured at prepare: the size of the second correction
+// per unit of the first, which overstates the error left by the first about
+// threefold) is below kRefineTol1; after correction k >= 2, once the estimated
+// relative error ratio_k^2 / ratio_{k-1} (linear convergence) is below
+// kRefineTol.
 constexpr float kRefineTol = 1e-12f;
-constexpr float kRefineTol1 = 2.5e-12f;
+constexpr float kRefineTol1 = 4e-12f;
 constexpr int kRefineCap = 4;
 
 // max over columns of (max|d| / max|x|) over the whole cluster; every thread of
@@ -390,7 +391,8 @@ __device__ __forceinline__ void correction_update(float2 (&g)[TT / 2], float2 (&
 // once to binary64; then the next item's F into g, row pair by row pair.
 template <int TT, bool SM, bool FUSED>
 __device__ __forceinline__ void output(float2 (&g)[TT / 2], const float2 (&xh)[TT / 2], const float* xlp, const float* cb,
-                                       float xL, float xR, const Rows<double>& x, const Rows<const float>& fn) {
+                                       float xL, float xR, const Rows<double>& x, const Rows<const float>& fn,
+                                       float& maxd) {
   constexpr int H = TT / 2;
   const float2 xL2 = f2dup(xL), xR2 = f2dup(xR);
 #pragma unroll
@@ -399,6 +401,7 @@ __device__ __forceinline__ void output(float2 (&g)[TT / 2], const float2 (&xh)[T
     if (FUSED) {
       const float4 ph = tld4<SM>(cb + j * kRefTP + kRT_PLH);
       const float2 d = f2fma(hi2(ph), xR2, f2fma(lo2(ph), xL2, g[j]));
+      maxd = fmaxf(maxd, fmaxf(fabsf(d.x), fabsf(d.y)));
       const df2 s = two_sum2(hi, d);
       hi = s.h;
       lo = f2add(lo, s.l);
@@ -412,8 +415,9 @@ __device__ __forceinline__ void output(float2 (&g)[TT / 2], const float2 (&xh)[T
 // Shared-memory layout of the refined kernel (byte offsets; the same function
 // sizes the launch on the host).
 struct RefOffsets {
-  size_t tab, xl, edge, red, cvg, iface, bytes;
+  size_t tab, xl, edge, red, cvg, ver, iface, bytes;
 };
+constexpr int kVerSlots = 4;   // rotating slots of speculative tiles' maxima
 __host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, bool sm_coef) {
   const size_t MM = (size_t)(NT / R);
   RefOffsets o{};
@@ -423,9 +427,39 @@ __host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, b
   o.edge = p; p += round16(4 * 4 * MM * R);
   o.red = p; p += round16(4 * 2 * (size_t)(NT / 32) * R);
   o.cvg = p; p += round16(4 * 5 * (size_t)R);
+  o.ver = p; p += round16(4 * (kVerSlots * 2 + 1) * (size_t)R);
   o.iface = p; p += iface_offsets(R, (int)MM, true).bytes;
   o.bytes = p;
   return o;
+}
+
+// Modes of a work item.
+//   kFixed   exactly `steps` corrections, the last one added in the output;
+//   kSpec    (per-tile test of a calibrated plan) one correction, added in the
+//            output at once; the tile's maxima go to a verification slot that
+//            the next work item's first interface exchange publishes, and
+//            every CTA checks ratio_1 x contraction <= kRefineTol1 there; a
+//            tile that fails is solved again, as kRetry, right after;
+//   kTested  (per-tile test, uncalibrated) a cluster-wide test after every
+//            correction, after the first with the plan's contraction;
+//   kRetry   kTested without the first test (one correction was not enough);
+//   kCalib   kRefineCalibSteps corrections, every one's size recorded.
+enum { kFixed = 0, kSpec = 1, kTested = 2, kRetry = 3, kCalib = 4 };
+
+// ratio_1 of a speculative tile from every CTA's slot (after a cluster barrier
+// has published the slots): one warp per column, lanes 0-15 max|d|, 16-31
+// max|x|; scratch[col] receives the column's ratio.
+template <int R>
+__device__ __forceinline__ void verify_columns(const float* slot, int C, float* scratch) {
+  const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int col = threadIdx.x >> 5; col < R; col += nwarps) {
+    const int cc = lane & 15;
+    float v = cc < C ? ld_cluster_f32(slot + (lane >> 4) * R + col, (unsigned)cc) : 0.f;
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const float mx = __shfl_sync(0xffffffffu, v, 16);
+    if (lane == 0) scratch[col] = mx > 0.f ? v / mx : 0.f;
+  }
 }
 
 template <int R, int TT, int NT, int MINB, bool SM>
@@ -446,6 +480,8 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   float* const red = reinterpret_cast<float*>(smem_raw + O.red);     // [2][warps][R] per-warp maxima
   float* const cvg = reinterpret_cast<float*>(smem_raw + O.cvg);     // [2][2][R] per-CTA maxima, read remotely
   float* const cvg_scratch = cvg + 4 * R;                            // [R]
+  float* const ver = reinterpret_cast<float*>(smem_raw + O.ver);     // [kVerSlots][2][R] speculative tiles' maxima
+  float* const ver_scratch = ver + kVerSlots * 2 * R;                // [R]
   const IfaceDF<R, MM, true> f{smem_raw + O.iface};
   const unsigned c = cluster_rank();
   const int tid = threadIdx.x;
@@ -457,15 +493,44 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   float* const xlp = sxl + tid * XLS;
   // Threads past the CTA's blocks (bl >= m) only round the CTA up to whole
   // warps; they run the same code on zero coefficients and zero data.
+  for (int k = tid; k < kVerSlots * 2 * R; k += blockDim.x) ver[k] = 0.f;   // published by the first cluster barrier
 
+#define ITEMX(i, fld) (L.single ? L.one.fld : L.items[i].fld)
   float2 g[H], xh[H];
   int cur_series = -1;
   int parity = 0;
-  bool preloaded = false;   // g already holds this item's F (loaded during the previous output)
-  for (int it = cluster_id; it < L.nitems; it += nclusters) {
+  int preloaded_item = -1;  // the item whose F g holds (loaded during the previous output)
+  int next_main = cluster_id;
+  int pending = -1;         // a speculative item that failed its verification
+  int unverified = -1;      // the last speculative item, its maxima not checked yet
+  int vslot = 0;            // and its verification slot
+  int nspec = 0;            // speculative items so far (slot rotation)
+  while (true) {
+    int it;
+    bool retry = false;
+    if (pending >= 0) {
+      it = pending;
+      pending = -1;
+      retry = true;
+    } else if (next_main < L.nitems) {
+      it = next_main;
+      next_main += nclusters;
+    } else if (unverified >= 0) {   // the last speculative item: check it now
+      cluster_barrier();
+      verify_columns<R>(ver + vslot * 2 * R, L.C, ver_scratch);
+      __syncthreads();
+      float q = 0.f;
+      for (int k = 0; k < R; k++) q = fmaxf(q, ver_scratch[k]);
+      if (!(q * ITEMX(unverified, contraction) <= kRefineTol1)) pending = unverified;
+      unverified = -1;
+      __syncthreads();
+      continue;
+    } else {
+      break;
+    }
     // fields of the current item, read where they are used (kernel parameter
     // or work list; no address of the parameter is taken)
-#define ITEM(fld) (L.single ? L.one.fld : L.items[it].fld)
+#define ITEM(fld) ITEMX(it, fld)
     const int tile = L.single ? it : L.items[it].tile;
     const int M = ITEM(M);
     if (ITEM(series) != cur_series) {   // new series: ratios, products, coefficient rows
@@ -496,12 +561,13 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
     // this thread's rows of F (none for padding threads and missing columns)
     const Rows<const float> fr{ITEM(F) + row0 * ITEM(ldF) + col, (int)ITEM(ldF), active ? nrows : 0};
     const int steps_cfg = ITEM(steps);
-    const bool adaptive = steps_cfg == -1;
-    const bool calib = steps_cfg == kRefineCalib;
-    const bool track = adaptive || calib;
-    const int cap = adaptive ? kRefineCap : (calib ? kRefineCalibSteps : steps_cfg);
+    const int mode = retry ? kRetry
+                           : steps_cfg == kRefineCalib ? kCalib
+                           : steps_cfg == -1 ? (ITEM(contraction) < 1.f ? kSpec : kTested) : kFixed;
+    const bool track = mode == kTested || mode == kRetry || mode == kCalib;
+    const int cap = mode == kFixed ? steps_cfg : mode == kSpec ? 1 : mode == kCalib ? kRefineCalibSteps : kRefineCap;
 
-    if (!preloaded) load_rhs<TT>(g, fr);
+    if (preloaded_item != it) load_rhs<TT>(g, fr);
 
     // ---- first solve (A2-A5): x = (xh, xl) ------------------------------------
     float maxx = 0.f;
@@ -516,8 +582,16 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       backward_y<TT, SM>(g, cb);
       cluster_wait();
       iface_df_fold<R, MM, true, true>(f, L.C, c, parity);
+      // the exchange also published the last speculative tile's maxima
+      if (unverified >= 0) verify_columns<R>(ver + vslot * 2 * R, L.C, ver_scratch);
       __syncthreads();
       parity ^= 1;
+      if (unverified >= 0) {   // every CTA reaches the same verdict from the same maxima
+        float q = 0.f;
+        for (int k = 0; k < R; k++) q = fmaxf(q, ver_scratch[k]);
+        if (!(q * ITEMX(unverified, contraction) <= kRefineTol1)) pending = unverified;
+        unverified = -1;
+      }
       f2pair xL{0.f, 0.f}, xR{0.f, 0.f};
       if (blk_ok) {
         if (b >= 1) xL = iface_df_sep_pair<R, MM, true, true>(f, bl, r);
@@ -530,21 +604,18 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
     // ---- corrections: r = F - A x, d = solve(r), x += d ----------------------
     const int64_t ldX = ITEM(ldX);
     const Rows<double> xr{ITEM(X) + row0 * ldX + col, (int)ldX, active ? nrows : 0};
-    // the next item's F, loaded during the output
-    const int it2 = it + nclusters;
-    preloaded = it2 < L.nitems;
+    // the item that runs next, whose F the output loads
+    const int nxt = pending >= 0 ? pending : (next_main < L.nitems ? next_main : -1);
     Rows<const float> fn{ITEM(F), 0, 0};
-    if (preloaded) {
-#define ITEM2(fld) (L.single ? L.one.fld : L.items[it2].fld)
-      const int tile_n = L.single ? it2 : L.items[it2].tile;
+    if (nxt >= 0) {
+      const int tile_n = L.single ? nxt : L.items[nxt].tile;
       const int64_t col_n = (int64_t)tile_n * R + r;
-      const int n_n = ITEM2(n);
-      if ((bl < m) && (b < ITEM2(M)) && col_n < ITEM2(N)) {
+      const int n_n = ITEMX(nxt, n);
+      if ((bl < m) && (b < ITEMX(nxt, M)) && col_n < ITEMX(nxt, N)) {
         fn.rows = (int)((n_n - row0) < TT ? (n_n - row0) : TT);
-        fn.ld32 = (int)ITEM2(ldF);
-        fn.base = ITEM2(F) + row0 * ITEM2(ldF) + col_n;
+        fn.ld32 = (int)ITEMX(nxt, ldF);
+        fn.base = ITEMX(nxt, F) + row0 * ITEMX(nxt, ldF) + col_n;
       }
-#undef ITEM2
     }
     float ratio_prev = 1.f;
     int done = 0;
@@ -559,23 +630,27 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       // Tests read every CTA's maxima of the last correction: a full cluster
       // barrier, which also publishes the edge values.  Otherwise the interior
       // of the residual overlaps the edge-value barrier.
-      const bool test = track && done >= 1;
+      const bool test = track && done >= (mode == kRetry ? 2 : 1);
       if (test) {
         cluster_barrier();
         const float ratio = cluster_ratio<R>(cvg + (done & 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
-        if (calib && tid == 0 && c == 0) atomicMax(&g_tdm_calib[done - 1], __float_as_uint(ratio));
-        if (adaptive) {
+        if (mode == kCalib && tid == 0 && c == 0) atomicMax(&g_tdm_calib[done - 1], __float_as_uint(ratio));
+        if (mode != kCalib) {
           const bool stop = done == 1 ? ratio * ITEM(contraction) <= kRefineTol1
                                       : ratio * ratio <= kRefineTol * ratio_prev;
-          ratio_prev = ratio;
           if (stop) break;
         }
+        ratio_prev = ratio;
       } else {
+        if (mode == kRetry && done == 1)   // the ratio test of correction 2 needs ratio_1
+          ratio_prev = 0.f;
         cluster_arrive();
       }
       df2 E0, Elast;
       residual_interior<TT, SM>(g, xh, xlp, cb, E0, Elast);
       if (!test) cluster_wait();
+      if (mode == kRetry && done == 1)
+        ratio_prev = cluster_ratio<R>(cvg + (done & 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
       f2pair xm{0.f, 0.f}, xp{0.f, 0.f};   // x at rows row0-1 and row0+TT
       if (bl > 0) {
         xm = f2pair{eLh[(bl - 1) * R + r], eLl[(bl - 1) * R + r]};
@@ -609,8 +684,30 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       }
       done++;
       if (!track && done == cap) {   // the last correction is added in the output
-        output<TT, SM, true>(g, xh, xlp, cb, xL, xR, xr, fn);
+        float maxd = 0.f;
+        output<TT, SM, true>(g, xh, xlp, cb, xL, xR, xr, fn, maxd);
         fused_out = true;
+        if (mode == kSpec) {   // this CTA's per-column maxima into the tile's verification slot
+          const int slot = nspec % kVerSlots;
+          if (!col_ok) maxd = 0.f;
+          float md = maxd, mx = maxx;
+#pragma unroll
+          for (int o = R; o < 32; o <<= 1) {
+            md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          }
+          if ((tid & 31) < R) {
+            atomicMax(reinterpret_cast<unsigned*>(ver) + (slot * 2 + 0) * R + r, __float_as_uint(md));
+            atomicMax(reinterpret_cast<unsigned*>(ver) + (slot * 2 + 1) * R + r, __float_as_uint(mx));
+          }
+          // the slot two speculative tiles ahead: its last readers have passed
+          // at least one cluster barrier since
+          const int z = (nspec + 2) % kVerSlots;
+          if (tid < 2 * R) ver[z * 2 * R + tid] = 0.f;
+          unverified = it;
+          vslot = slot;
+          nspec++;
+        }
         break;
       }
       float maxd = 0.f;
@@ -625,13 +722,16 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       if (track && done == cap) {   // cap reached: record the last correction
         cluster_barrier();
         const float ratio = cluster_ratio<R>(cvg + (done & 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
-        if (calib && tid == 0 && c == 0) atomicMax(&g_tdm_calib[done - 1], __float_as_uint(ratio));
-        if (adaptive && tid == 0 && !(ratio * ratio <= kRefineTol * ratio_prev)) atomicExch(L.err, kDevErrNotConverged);
+        if (mode == kCalib && tid == 0 && c == 0) atomicMax(&g_tdm_calib[done - 1], __float_as_uint(ratio));
+        if (mode != kCalib && tid == 0 && !(ratio * ratio <= kRefineTol * ratio_prev)) atomicExch(L.err, kDevErrNotConverged);
       }
-      output<TT, SM, false>(g, xh, xlp, cb, 0.f, 0.f, xr, fn);
+      float unused = 0.f;
+      output<TT, SM, false>(g, xh, xlp, cb, 0.f, 0.f, xr, fn, unused);
     }
+    preloaded_item = nxt;
 #undef ITEM
   }
+#undef ITEMX
   // no CTA may leave while a peer can still read its shared memory
   cluster_barrier();
 }
