@@ -44,13 +44,19 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _kernel_hash() -> str:
+# the sources each captured kernel is built from (a capture is void once one changes)
+KERNEL_SOURCES = {
+    "k_refined": ("tdm_refine.cu", "tdm_refine.cuh", "tdm_f2.cuh", "tdm_df.cuh", "tdm_iface_df.cuh",
+                  "tdm_kernel_common.cuh", "tdm_internal.cuh", "tdm_tma.cuh"),
+}
+
+
+def _kernel_hash(kernel: str = "k_refined") -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0901_2859_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -61,7 +67,7 @@ def _traffic(kernel: str):
         with open(path) as f:
             t = json.load(f)
         e = t.get(kernel)
-        if e and e.get("source_hash") == _kernel_hash():
+        if e and e.get("source_hash") == _kernel_hash(kernel):
             return float(e["bytes_per_launch_full"])
     except Exception:
         pass

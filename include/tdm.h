@@ -244,12 +244,15 @@ tdm_status tdm_solve_batched_noalloc(const tdm_handle* hs, int count,
  * the same plan (Lemma 2).  With W = dL/dX and X the forward solution:
  *   dF = Lambda,  db_i = -sum_r Lambda_ir X_ir,
  *   da_i = -sum_r (Lambda_ir X_{i+1,r} + Lambda_{i+1,r} X_ir).
- *   W, X   device [n][ld], binary32 (TDM_FP32) or binary64 (TDM_FP64)
- *   dF     device [n][ld], same dtype; receives Lambda
+ *   W      device [n][ld]: binary64 (TDM_FP64), binary32 (TDM_FP32, TDM_FP32_REFINED)
+ *   X      device [n][ld]: the forward solution, binary64 (TDM_FP64, TDM_FP32_REFINED)
+ *          or binary32 (TDM_FP32)
+ *   dF     device [n][ld], the dtype of X; receives Lambda (for TDM_FP32_REFINED the
+ *          refined solve of W: binary64 accuracy at binary32 input)
  *   da, db device binary64 arrays of n-1 and n entries, or NULL to skip
  * The row sums over right-hand sides are accumulated in binary64 in a fixed
  * order (deterministic).
- * Errors: TDM_ERR_INVALID_ARG, TDM_ERR_NOT_IMPLEMENTED (TDM_FP32_REFINED), TDM_ERR_CUDA. */
+ * Errors: TDM_ERR_INVALID_ARG, TDM_ERR_NOT_IMPLEMENTED (general plans), TDM_ERR_CUDA. */
 tdm_status tdm_solve_backward(tdm_handle h, const void* W, const void* X, int64_t ld,
                               int64_t N, void* dF, double* da, double* db,
                               tdm_precision prec, void* stream);

@@ -132,12 +132,12 @@ class Plan:
                        need_ab: bool = True):
         """(dF, da, db) for L with dL/dX = W, X = A^{-1} F (adjoint solve, Lemma 2)."""
         ld = _check_rhs(W, self.n, _IN_DTYPE[precision], "W")
-        ldx = _check_rhs(X, self.n, _IN_DTYPE[precision], "X")
+        ldx = _check_rhs(X, self.n, _OUT_DTYPE[precision], "X")
         N = int(W.shape[1])
         if ld != ldx:
             W, X = W.contiguous(), X.contiguous()
             ld = max(N, 1)
-        dF = torch.empty_strided((self.n, N), (ld, 1), dtype=W.dtype, device=W.device)
+        dF = torch.empty_strided((self.n, N), (ld, 1), dtype=_OUT_DTYPE[precision], device=W.device)
         da = torch.empty(max(self.n - 1, 0), dtype=torch.float64, device=W.device) if need_ab else None
         db = torch.empty(self.n, dtype=torch.float64, device=W.device) if need_ab else None
         with torch.cuda.device(self.device):
@@ -254,7 +254,10 @@ class TDMSolve(torch.autograd.Function):
     def backward(ctx, gX):
         (X,) = ctx.saved_tensors
         need_ab = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
-        dF, da, db = ctx.plan.solve_backward(gX.contiguous().to(X.dtype), X, ctx.precision, need_ab=need_ab)
+        # W takes the forward input's dtype (binary32 for the refined solve, whose X is binary64)
+        dF, da, db = ctx.plan.solve_backward(gX.contiguous().to(_IN_DTYPE[ctx.precision]), X, ctx.precision,
+                                             need_ab=need_ab)
+        dF = dF.to(_IN_DTYPE[ctx.precision])
         da = da.to(ctx.plan.a.dtype) if (da is not None and ctx.needs_input_grad[1]) else None
         db = db.to(ctx.plan.b.dtype) if (db is not None and ctx.needs_input_grad[2]) else None
         return dF, da, db, None, None

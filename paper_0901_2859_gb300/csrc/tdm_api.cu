@@ -155,7 +155,7 @@ tdm_status tdm_launch_backward_sums(tdm_plan_s* p, const void* W, const void* X,
   if (!da && !db) return TDM_OK;
   const int64_t n = p->n;
   int grid = n < 65536 ? (int)n : 65536;
-  if (prec == TDM_FP64)
+  if (prec != TDM_FP32)   // Lambda and X in binary64 (the binary64 and the refined solves)
     k_grad_rows<double><<<grid, 256, 0, s>>>(static_cast<const double*>(W), static_cast<const double*>(X),
                                              ld, N, n, da, db);
   else
@@ -201,8 +201,7 @@ extern "C" tdm_status tdm_solve_backward(tdm_handle h, const void* W, const void
                                          int64_t N, void* dF, double* da, double* db,
                                          tdm_precision prec, void* stream) {
   if (!h) return TDM_ERR_INVALID_ARG;
-  if (prec == TDM_FP32_REFINED) return TDM_ERR_NOT_IMPLEMENTED;
-  if (prec != TDM_FP64 && prec != TDM_FP32) return TDM_ERR_INVALID_ARG;
+  if (prec != TDM_FP64 && prec != TDM_FP32 && prec != TDM_FP32_REFINED) return TDM_ERR_INVALID_ARG;
   if (h->general) return TDM_ERR_NOT_IMPLEMENTED;   // the adjoint of a nonsymmetric A is another matrix
   if (N < 0 || ld < N) return TDM_ERR_INVALID_ARG;
   if (N == 0) {
@@ -217,7 +216,7 @@ extern "C" tdm_status tdm_solve_backward(tdm_handle h, const void* W, const void
     return TDM_ERR_INVALID_ARG;
   tdm_status st = validate_solve(h, W, ld, dF, ld, N, prec);
   if (st != TDM_OK) return st;
-  const size_t bytes = ((size_t)(h->n - 1) * (size_t)ld + (size_t)N) * elem_in(prec);
+  const size_t bytes = ((size_t)(h->n - 1) * (size_t)ld + (size_t)N) * elem_out(prec);   // X and dF
   if (overlaps(X, bytes, dF, bytes)) return TDM_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   cudaStream_t s = (cudaStream_t)stream;
