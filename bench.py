@@ -501,14 +501,15 @@ def run_large(args):
 
 def run_algorithm2(args):
     """Algorithm 2 (Section 3.1) at the benchmark size: every separator value of
-    the precision series (P = M - 1 = 511 components) as G^T F, in binary64 and
-    as three TF32 tensor-core products; the dichotomy's own separator values are
-    the reference."""
+    the precision series (P = M - 1 = 511 components) as G^T F, by the library's
+    tensor-core kernel (three TF32 products, tcgen05) and in binary64; the
+    dichotomy's own separator values are the reference.  For context, the same
+    three TF32 products as cuBLAS GEMMs."""
     import numpy as np
     import torch
     import paper_0901_2859_gb300 as tdm
     from paper_0901_2859_gb300 import workloads
-    from paper_0901_2859_gb300.algorithm2 import components, inverse_rows
+    from paper_0901_2859_gb300.algorithm2 import _tf32_split, components, inverse_rows
 
     dev = torch.device("cuda", DIST["local"])
     torch.cuda.set_device(dev)
@@ -522,20 +523,36 @@ def run_algorithm2(args):
     steps = max(3, min(args.steps, 10))
     G = inverse_rows(plan, ks)
     ms_g = _events_time(lambda: inverse_rows(plan, ks), steps, 3, torch)
+
+    def cublas_tf32x3():   # context only: library GEMMs on the same split operands
+        gh, gt = _tf32_split(G.t().to(torch.float32).contiguous())
+        fh, ft = _tf32_split(F)
+        X = torch.matmul(gh, fh)
+        X += torch.matmul(gh, ft)
+        X += torch.matmul(gt, fh)
+        return X
+
     out = {}
-    for mode in ("tf32x3", "fp64"):
-        ms = _events_time(lambda: components(plan, F, ks, mode, G=G), steps if mode == "tf32x3" else 3, 3, torch)
-        X = components(plan, F, ks, mode, G=G).double()
+    for mode, fn, k in (("tc", lambda: components(plan, F, ks, "tc", G=G), steps),
+                        ("fp64", lambda: components(plan, F, ks, "fp64", G=G), 3),
+                        ("cublas_tf32x3", cublas_tf32x3, steps)):
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = mode == "cublas_tf32x3"
+        try:
+            ms = _events_time(fn, k, 3, torch)
+            X = fn().double()
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
         err = float(((X - ref).abs().amax(dim=1) / ref.abs().amax(dim=1)).max())
-        flops = 2.0 * len(ks) * n * N * (3 if mode == "tf32x3" else 1)
+        flops = 2.0 * len(ks) * n * N * (1 if mode == "fp64" else 3)
         out[mode] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12, "rel_err_vs_dichotomy": err}
     plan.close()
     line = {
-        "metric": "separator values by Algorithm 2 (dense G^T F)", "value": out["tf32x3"]["ms"], "unit": "ms",
-        "n_gpus": DIST["world"], "steps": steps, "warmup": 3, "ms_per_step": out["tf32x3"]["ms"],
+        "metric": "separator values by Algorithm 2 (dense G^T F)", "value": out["tc"]["ms"], "unit": "ms",
+        "n_gpus": DIST["world"], "steps": steps, "warmup": 3, "ms_per_step": out["tc"]["ms"],
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
         "config": {"workload": f"algorithm2: precision series n={n} N={N}, {len(ks)} separator components",
-                   "components": len(ks)},
+                   "components": len(ks), "kernel": "k_alg2_tc (tcgen05.mma kind::tf32, split-K 1024)"},
         "paths": out, "inverse_rows_ms": ms_g,
     }
     if DIST["rank"] == 0:

@@ -43,6 +43,7 @@
 #ifndef TDM_H
 #define TDM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -256,6 +257,34 @@ tdm_status tdm_solve_batched_noalloc(const tdm_handle* hs, int count,
 tdm_status tdm_solve_backward(tdm_handle h, const void* W, const void* X, int64_t ld,
                               int64_t N, void* dF, double* da, double* db,
                               tdm_precision prec, void* stream);
+
+/* tdm_algorithm2 -- Algorithm 2 (Section 3.1): selected components of every
+ * solution as dense products, X[k][r] = sum_i G_k(i) F[i][r] for P components
+ * k, with G_k = A^{-1} e_k the inverse rows (eq. green_v, Lemma 2; a caller
+ * obtains them from tdm_solve on unit right-hand sides).  The product runs on
+ * the tensor cores (tcgen05.mma, TF32 inputs, binary32 accumulation in tensor
+ * memory) as three TF32 products of the operands' TF32 heads and binary32
+ * tails; each binary32 accumulation covers at most 1024 rows of K, and the
+ * partial sums are added in binary32 pairs.
+ *   G     device, [n][ldG] binary64: column k is G_k (ldG >= P)
+ *   F     device, [n][ldF] binary32 right-hand sides; 16-byte aligned, ldF a
+ *         multiple of 4
+ *   X     device, [P][ldX] binary32, receives the components (ldX >= N)
+ *   work  device workspace of at least tdm_algorithm2_workspace(min(P, 512), n, N)
+ *         bytes, 256-byte aligned; calls that share it must be ordered
+ * Components are processed 512 at a time.  Asynchronous on `stream`; a bounded
+ * device wait that gave up is reported by tdm_algorithm2_status.
+ * Errors: TDM_ERR_INVALID_ARG (sizes, strides, alignment, workspace too small),
+ * TDM_ERR_NOT_IMPLEMENTED (F cannot be described to the copy engine),
+ * TDM_ERR_CUDA. */
+size_t tdm_algorithm2_workspace(int64_t P, int64_t n, int64_t N);
+tdm_status tdm_algorithm2(const double* G, int64_t ldG, int64_t P, int64_t n, const float* F, int64_t ldF,
+                          int64_t N, float* X, int64_t ldX, void* work, size_t work_bytes, void* stream);
+/* tdm_algorithm2_status -- the device error word of the last tdm_algorithm2 call
+ * with this workspace and sizes (0 = none, 1 = a bounded wait gave up);
+ * synchronizes the stream. */
+tdm_status tdm_algorithm2_status(const void* work, int64_t P, int64_t n, int64_t N, void* stream,
+                                 int* device_error);
 
 /* tdm_selftest_wait_timeout -- a check of the failure path of the solve
  * kernels' bounded waits (no counterpart in the paper): one CTA waits on an

@@ -18,7 +18,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_refined": 2}
 # every symbol include/tdm.h declares
 EXPORTS = ("tdm_prepare", "tdm_prepare_general", "tdm_solve", "tdm_solve_host", "tdm_solve_batched", "tdm_solve_batched_noalloc",
            "tdm_solve_backward", "tdm_selftest_wait_timeout", "tdm_get_info", "tdm_destroy",
-           "tdm_status_string")
+           "tdm_status_string", "tdm_algorithm2_workspace", "tdm_algorithm2", "tdm_algorithm2_status")
 NOALLOC_MAX_TILES = 4096   # TDM_NOALLOC_MAX_TILES
 
 
@@ -76,9 +76,13 @@ def load(build_if_missing: bool = True):
         lib.tdm_selftest_wait_timeout.argtypes = [i64, vp]
         lib.tdm_destroy.argtypes = [vp]
         lib.tdm_status_string.argtypes = [i32]
+        lib.tdm_algorithm2_workspace.argtypes = [i64, i64, i64]
+        lib.tdm_algorithm2.argtypes = [vp, i64, i64, i64, vp, i64, i64, vp, i64, vp, ctypes.c_size_t, vp]
+        lib.tdm_algorithm2_status.argtypes = [vp, i64, i64, i64, vp, ctypes.POINTER(i32)]
         for name in EXPORTS:
             getattr(lib, name).restype = ctypes.c_int
         lib.tdm_status_string.restype = ctypes.c_char_p
+        lib.tdm_algorithm2_workspace.restype = ctypes.c_size_t
         _lib = lib
         return lib
 
