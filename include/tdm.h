@@ -194,15 +194,39 @@ tdm_status tdm_solve_host(tdm_handle h, const void* F, int64_t ldF, void* X, int
 
 /* tdm_solve_batched -- many distinct constant matrices, each with its own
  * block of right-hand sides (the per-mode series of the Fourier method,
- * Section 4, eqs. series_fft, poisson_end), in one persistent launch.
+ * Section 4, eqs. series_fft, poisson_end), by the refined persistent kernel
+ * in the layout tdm_set_batched_strategy selects.
  *   hs[k], F[k], ldF[k], X[k], ldX[k], N[k] for k = 0..count-1, with the same
  *   meaning as for tdm_solve (host arrays of device pointers).  All plans must
- *   have the same block_rows.  The launch captures cleanly in a CUDA graph.
+ *   have the same block_rows.  Work lists are built and uploaded on the first
+ *   call with an argument set and kept until one of its plans is destroyed;
+ *   later calls (and CUDA-graph replays of a captured call) upload nothing.
  * Errors: as tdm_solve, plus TDM_ERR_INVALID_ARG for mixed block_rows. */
 tdm_status tdm_solve_batched(const tdm_handle* hs, int count,
                              const void* const* F, const int64_t* ldF,
                              void* const* X, const int64_t* ldX, const int64_t* N,
                              tdm_precision prec, void* stream);
+
+/* tdm_set_batched_strategy -- how tdm_solve_batched lays out refined work,
+ * process-wide, from the next call on:
+ *   3  (default) by rule: 0 when the batch needs at most four launch classes
+ *      (kernel shape and cluster width), else 2;
+ *   2  one single-series launch per series, biggest first, round robin over
+ *      the caller's stream and three helper streams that fork from it and
+ *      join it again;
+ *   0  one persistent launch per kernel shape and cluster width over a work
+ *      list of tiles (a cluster takes one tile of one series at a time),
+ *      spread over the same streams;
+ *   1  one persistent launch per kernel shape and correction schedule: the
+ *      clusters are as wide as the widest series needs, and each walks a list
+ *      of units in which tiles of several series run side by side, each on an
+ *      aligned power-of-two group of CTAs.
+ * Under each, a series with a fixed or calibrated refinement gets the result
+ * of its own tdm_solve, bit for bit; under 1, a plan with the uncalibrated
+ * per-tile test (refine_steps = -1 requested), and a unit whose speculative
+ * check fails, run four corrections and a convergence check.
+ * Errors: TDM_ERR_INVALID_ARG for any other value. */
+tdm_status tdm_set_batched_strategy(int strategy);
 
 /* tdm_solve_batched_noalloc -- tdm_solve_batched with TDM_FP32_REFINED for
  * callers that must not allocate: the call allocates no device or host memory

@@ -7,8 +7,8 @@ products, separator values by the main parallel sweep theorem, local sweeps
 with a correction), all as CUDA kernels for sm_103a behind the C ABI in
 ``include/tdm.h``.  This package is the thin Python binding over that ABI.
 """
-from .api import Plan, TDMError, TDMSolve, prepare, prepare_general, solve_batched, solve_batched_noalloc, tdm_solve  # noqa: F401
+from .api import Plan, TDMError, TDMSolve, prepare, prepare_general, set_batched_strategy, solve_batched, solve_batched_noalloc, tdm_solve  # noqa: F401
 from ._build import build  # noqa: F401
 from . import autotune  # noqa: F401
 
-__all__ = ["Plan", "TDMError", "TDMSolve", "prepare", "prepare_general", "solve_batched", "solve_batched_noalloc", "tdm_solve", "build"]
+__all__ = ["Plan", "TDMError", "TDMSolve", "prepare", "prepare_general", "set_batched_strategy", "solve_batched", "solve_batched_noalloc", "tdm_solve", "build"]

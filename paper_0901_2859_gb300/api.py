@@ -187,8 +187,22 @@ def prepare(a, b, block_rows: int = 0, refine_steps: int = 0, device=None, tile_
     return Plan(a, b, block_rows=block_rows, refine_steps=refine_steps, tile_rhs=tile_rhs)
 
 
+BATCHED_STRATEGIES = {"by_width": 0, "grouped": 1, "per_series": 2, "auto": 3}
+
+
+def set_batched_strategy(strategy: str) -> None:
+    """How ``solve_batched`` lays out refined work (``tdm_set_batched_strategy``):
+    "auto" (default) -- "by_width" for batches needing at most four launch
+    classes, else "per_series"; "per_series" -- one single-series launch per
+    series over four streams; "by_width" -- one persistent launch per kernel
+    shape and cluster width; "grouped" -- one per kernel shape, tiles of
+    several series side by side in each cluster."""
+    check(_lib.load().tdm_set_batched_strategy(BATCHED_STRATEGIES[strategy]), "tdm_set_batched_strategy")
+
+
 def solve_batched(plans, Fs, precision: str = "fp32_refined", outs=None):
-    """Solve every plans[k] against Fs[k] in one call (one persistent launch)."""
+    """Solve every plans[k] against Fs[k] in one call (persistent launches over
+    a device-resident work list; see ``set_batched_strategy``)."""
     if len(plans) != len(Fs):
         raise ValueError("plans and Fs must have the same length")
     count = len(plans)

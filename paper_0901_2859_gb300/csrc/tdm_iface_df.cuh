@@ -380,16 +380,18 @@ __device__ __forceinline__ void iface_push_fold(const IfaceDF<R, MM, false>& f, 
 
 // in_R, in_L of every column from the other CTAs' totals (after a cluster
 // barrier): one warp per column, lanes 0-15 for the CTAs to the left, 16-31
-// for those to the right.
+// for those to the right.  The C CTAs that share the tile are cluster ranks
+// base .. base + C - 1; c is this CTA's place among them.
 template <int R, int MM, bool PAIR = true, bool AP = PAIR>
-__device__ __forceinline__ void iface_df_fold(const IfaceDF<R, MM, PAIR>& f, int C, unsigned c, int parity) {
+__device__ __forceinline__ void iface_df_fold(const IfaceDF<R, MM, PAIR>& f, int C, unsigned c, int parity,
+                                              unsigned base = 0) {
   const int lane = threadIdx.x & 31, cc = lane & 15;
   const bool left = lane < 16;
   const bool valid = left ? (cc < (int)c) : (cc > (int)c && cc < C);
   for (int r = threadIdx.x >> 5; r < R; r += blockDim.x >> 5) {
     f2pair v{0.f, 0.f};
     if (valid) {
-      const float2 x = ld_cluster_f32x2(f.xch() + (parity * 2 + (left ? 0 : 1)) * R + r, (unsigned)cc);
+      const float2 x = ld_cluster_f32x2(f.xch() + (parity * 2 + (left ? 0 : 1)) * R + r, base + (unsigned)cc);
       v = mfma<AP>(mld<AP>(left ? &f.wR()[cc] : &f.wL()[cc]), fp(x), f2pair{0.f, 0.f});
     }
 #pragma unroll

@@ -150,7 +150,7 @@ extern "C" tdm_status tdm_solve_batched_noalloc(const tdm_handle* hs, int count,
   int nitems = 0;
   for (int i = 0; i < ne; i++) {
     const Entry& e = g_entries[i];
-    RefItem base = tdm_refined_item(hs[e.k], F[e.k], ldF[e.k], X[e.k], ldX[e.k], N[e.k], e.k);
+    RefItem base = tdm_refined_item(hs[e.k], F[e.k], ldF[e.k], X[e.k], ldX[e.k], N[e.k], e.k, e.sh);
     for (int tile = 0; tile < e.tiles; tile++) {
       base.tile = tile;
       g_stage[nitems++] = base;

@@ -491,7 +491,7 @@ tdm_status calibrate_refinement(tdm_plan_s* p, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     if (st == TDM_OK) {
       k_calib_rhs<<<128, 256, 0, s>>>(F, p->n * N, 0x9e3779b9u);
-      RefItem one = tdm_refined_item(p, F, N, X, N, N, 0);
+      RefItem one = tdm_refined_item(p, F, N, X, N, N, 0, sh);
       one.steps = kRefineCalib;
       st = tdm_refined_launch(sh, p->t, nullptr, &one, (N + sh.R - 1) / sh.R, p->dev_err, s);
     }

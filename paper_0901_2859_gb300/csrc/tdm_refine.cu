@@ -76,35 +76,57 @@ constexpr float kRefineTol = 1e-12f;
 constexpr float kRefineTol1 = 4e-12f;
 constexpr int kRefineCap = 4;
 
-// max over columns of (max|d| / max|x|) over the whole cluster; every thread of
-// every CTA gets the same value (exact maxima, the same division).  slot holds
-// this CTA's per-column maxima [2][R]; one warp per column reads every CTA's
-// pair in one round (lanes 0-15: max|d|, lanes 16-31: max|x|).
-template <int R>
-__device__ __forceinline__ float cluster_ratio(const float* slot, int C, int tid, float* scratch, float* bcast) {
-  const int lane = tid & 31, nwarps = blockDim.x >> 5;
-  for (int col = tid >> 5; col < R; col += nwarps) {
-    const int cc = lane & 15;
-    float v = cc < C ? ld_cluster_f32(slot + (lane >> 4) * R + col, (unsigned)cc) : 0.f;
+// Slots of per-CTA maxima that the other CTAs of the cluster read: [2][R]
+// (max|d| and max|x| of every column), then the size of the CTA's group and
+// its item's contraction.
+__host__ __device__ constexpr int kSlot(int R) { return 2 * R + 2; }
+
+// Relative size max|d| / max|x| of every column for each group of CTAs (the
+// maxima taken over the group's CTAs), times the group's contraction when
+// `scale`: out[col] receives the largest over the groups of the cluster
+// (every CTA computes the same value from the same maxima), own[col] (if not
+// null) the value of this CTA's group.  Groups are aligned rank ranges of a
+// power-of-two size, or a single group of all CTAs from rank 0, so that the
+// xor-shuffles below stay inside a group.  One warp per column: lanes 0-15
+// read CTA lane's max|d|, lanes 16-31 CTA (lane - 16)'s max|x|; the slots
+// must have been published by a cluster barrier.
+// Without groups (GROUPED false) every CTA belongs to the one group of all CL
+// CTAs and shares the contraction kc0: nothing but the maxima is read.
+template <int R, bool GROUPED>
+__device__ __forceinline__ void group_ratios(const float* slot, int CL, unsigned cphys, bool scale, float kc0,
+                                             float* out, float* own) {
+  const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const unsigned cc = lane & 15;
+  const bool have = (int)cc < CL;
+  int gs = CL;
+  float kc = scale ? kc0 : 1.f;
+  if constexpr (GROUPED) {
+    gs = have ? (int)ld_cluster_f32(slot + 2 * R, cc) : 1;
+    kc = have && scale ? ld_cluster_f32(slot + 2 * R + 1, cc) : 1.f;
+  }
+  for (int col = threadIdx.x >> 5; col < R; col += nwarps) {
+    float v = have ? ld_cluster_f32(slot + (lane >> 4) * R + col, cc) : 0.f;
 #pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const float mx = __shfl_sync(0xffffffffu, v, 16);
-    if (lane == 0) scratch[col] = mx > 0.f ? v / mx : 0.f;
+    for (int o = 8; o >= 1; o >>= 1) {
+      const float w = __shfl_xor_sync(0xffffffffu, v, o);
+      if (o < gs) v = fmaxf(v, w);
+    }
+    const float mx = __shfl_down_sync(0xffffffffu, v, 16);
+    float q = (lane < 16 && mx > 0.f) ? v / mx * kc : 0.f;
+    const float mine = __shfl_sync(0xffffffffu, q, (int)cphys);
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) q = fmaxf(q, __shfl_xor_sync(0xffffffffu, q, o));
+    if (lane == 0) {
+      out[col] = q;
+      if (own) own[col] = mine;
+    }
   }
-  __syncthreads();
-  if (tid == 0) {
-    float q = 0.f;
-    for (int k = 0; k < R; k++) q = fmaxf(q, scratch[k]);
-    *bcast = q;
-  }
-  __syncthreads();
-  return *bcast;
 }
 
-// per-CTA, per-column maxima of |d| and |x| into slot [2][R]: shuffles over
-// the blocks a warp covers, then over the warps
+// per-CTA, per-column maxima of |d| and |x| into slot (layout of kSlot):
+// shuffles over the blocks a warp covers, then over the warps
 template <int R>
-__device__ __forceinline__ void cta_maxima(float md, float mx, float* red, float* slot, int tid) {
+__device__ __forceinline__ void cta_maxima(float md, float mx, float* red, float* slot, int tid, int gs, float kc) {
   const int lane = tid & 31, nwarps = blockDim.x >> 5;
 #pragma unroll
   for (int o = R; o < 32; o <<= 1) {
@@ -124,6 +146,10 @@ __device__ __forceinline__ void cta_maxima(float md, float mx, float* red, float
     }
     slot[tid] = a;
     slot[R + tid] = b;
+  }
+  if (tid == 0) {
+    slot[2 * R] = (float)gs;
+    slot[2 * R + 1] = kc;
   }
 }
 
@@ -426,8 +452,8 @@ __host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, b
   o.xl = p; p += round16(4 * (size_t)NT * (TT + 2));
   o.edge = p; p += round16(4 * 4 * MM * R);
   o.red = p; p += round16(4 * 2 * (size_t)(NT / 32) * R);
-  o.cvg = p; p += round16(4 * 5 * (size_t)R);
-  o.ver = p; p += round16(4 * (kVerSlots * 2 + 1) * (size_t)R);
+  o.cvg = p; p += round16(4 * (4 * (size_t)kSlot(R) + 2 * (size_t)R));
+  o.ver = p; p += round16(4 * (kVerSlots * (size_t)kSlot(R) + (size_t)R));
   o.iface = p; p += iface_offsets(R, (int)MM, true).bytes;
   o.bytes = p;
   return o;
@@ -437,40 +463,35 @@ __host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, b
 //   kFixed   exactly `steps` corrections, the last one added in the output;
 //   kSpec    (per-tile test of a calibrated plan) one correction, added in the
 //            output at once; the tile's maxima go to a verification slot that
-//            the next work item's first interface exchange publishes, and
-//            every CTA checks ratio_1 x contraction <= kRefineTol1 there; a
-//            tile that fails is solved again, as kRetry, right after;
+//            the next unit's first interface exchange publishes, and every CTA
+//            checks ratio_1 x contraction <= kRefineTol1 there for every
+//            group; a unit that fails is solved again right after (kRetry, or
+//            kRetryFixed in a grouped launch);
 //   kTested  (per-tile test, uncalibrated) a cluster-wide test after every
 //            correction, after the first with the plan's contraction;
 //   kRetry   kTested without the first test (one correction was not enough);
-//   kCalib   kRefineCalibSteps corrections, every one's size recorded.
-enum { kFixed = 0, kSpec = 1, kTested = 2, kRetry = 3, kCalib = 4 };
+//   kCalib   kRefineCalibSteps corrections, every one's size recorded;
+//   kRetryFixed  (grouped launches, whose groups must all pass the same
+//            cluster barriers) kRefineCap corrections, every one's maxima
+//            kept; at the end, per group, the tested criterion must hold
+//            between some two consecutive corrections.
+enum { kFixed = 0, kSpec = 1, kTested = 2, kRetry = 3, kCalib = 4, kRetryFixed = 5 };
 
-// ratio_1 of a speculative tile from every CTA's slot (after a cluster barrier
-// has published the slots): one warp per column, lanes 0-15 max|d|, 16-31
-// max|x|; scratch[col] receives the column's ratio.
-template <int R>
-__device__ __forceinline__ void verify_columns(const float* slot, int C, float* scratch) {
-  const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int col = threadIdx.x >> 5; col < R; col += nwarps) {
-    const int cc = lane & 15;
-    float v = cc < C ? ld_cluster_f32(slot + (lane >> 4) * R + col, (unsigned)cc) : 0.f;
-#pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const float mx = __shfl_sync(0xffffffffu, v, 16);
-    if (lane == 0) scratch[col] = mx > 0.f ? v / mx : 0.f;
-  }
-}
+// Launch modes: one series (its tile i is unit i); a list of items, one per
+// unit, every CTA of the cluster on it (items of one cluster width, each with
+// its own blocks per CTA); grouped units (an item per CTA).
+enum { kLaunchSingle = 0, kLaunchList = 1, kLaunchGrouped = 2 };
 
-template <int R, int TT, int NT, int MINB, bool SM>
+template <int R, int TT, int NT, int MINB, bool SM, int LM>
 __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   constexpr int H = TT / 2;
   constexpr int MM = NT / R;                               // most blocks a CTA can own
   constexpr int STR = kRefTabStride(TT);
   constexpr int XLS = TT + 2;                              // floats per thread of xl (conflict-free float2 rows)
+  constexpr int SL = kSlot(R);
   constexpr RefOffsets O = refine_offsets(R, TT, NT, SM);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float ratio_s;
+  __shared__ RefItem s_item;                                         // the current item (list, grouped)
   float* const stab = reinterpret_cast<float*>(smem_raw + O.tab);    // [MM][STR] coefficient table
   float* const sxl = reinterpret_cast<float*>(smem_raw + O.xl);      // [NT][XLS] low words of x
   float* const eFh = reinterpret_cast<float*>(smem_raw + O.edge);    // [4][MM][R] block edge values of x
@@ -478,64 +499,106 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   float* const eLh = eFl + MM * R;
   float* const eLl = eLh + MM * R;
   float* const red = reinterpret_cast<float*>(smem_raw + O.red);     // [2][warps][R] per-warp maxima
-  float* const cvg = reinterpret_cast<float*>(smem_raw + O.cvg);     // [2][2][R] per-CTA maxima, read remotely
-  float* const cvg_scratch = cvg + 4 * R;                            // [R]
-  float* const ver = reinterpret_cast<float*>(smem_raw + O.ver);     // [kVerSlots][2][R] speculative tiles' maxima
-  float* const ver_scratch = ver + kVerSlots * 2 * R;                // [R]
+  float* const cvg = reinterpret_cast<float*>(smem_raw + O.cvg);     // [4][SL] maxima of corrections, read remotely
+  float* const cvg_all = cvg + 4 * SL;                               // [R] largest ratio over the groups
+  float* const cvg_own = cvg_all + R;                                // [R] ratio of this CTA's group
+  float* const ver = reinterpret_cast<float*>(smem_raw + O.ver);     // [kVerSlots][SL] speculative units' maxima
+  float* const ver_all = ver + kVerSlots * SL;                       // [R]
   const IfaceDF<R, MM, true> f{smem_raw + O.iface};
-  const unsigned c = cluster_rank();
+  const unsigned cphys = cluster_rank();
   const int tid = threadIdx.x;
   const int r = tid % R;
   const int bl = tid / R;
-  const int m = L.m;
-  const int cluster_id = blockIdx.x / L.C;
-  const int nclusters = gridDim.x / L.C;
+  const int CL = L.C;
+  const int cluster_id = blockIdx.x / CL;
+  const int nclusters = gridDim.x / CL;
+  constexpr bool grouped = LM == kLaunchGrouped;
   float* const xlp = sxl + tid * XLS;
   // Threads past the CTA's blocks (bl >= m) only round the CTA up to whole
   // warps; they run the same code on zero coefficients and zero data.
-  for (int k = tid; k < kVerSlots * 2 * R; k += blockDim.x) ver[k] = 0.f;   // published by the first cluster barrier
+  for (int k = tid; k < kVerSlots * SL; k += blockDim.x) ver[k] = 0.f;   // published by the first cluster barrier
 
-#define ITEMX(i, fld) (L.single ? L.one.fld : L.items[i].fld)
+#define ITEMX(i, fld) (LM == kLaunchSingle ? L.one.fld : L.items[i].fld)
+  // the item this CTA works on in unit u, and the first rank of its group
+  auto item_of = [&](int u) -> int { return grouped ? L.units[u * kUnitW + cphys] : u; };
+  auto group_base = [&](int gs) -> unsigned { return grouped ? (cphys & ~(unsigned)(gs - 1)) : 0u; };
+  // largest ratio over the groups (every CTA the same) and this CTA's group's
+  auto ratios = [&](const float* slot, float& own) -> float {
+    group_ratios<R, grouped>(slot, CL, cphys, false, 1.f, cvg_all, cvg_own);
+    __syncthreads();
+    float q = 0.f, o = 0.f;
+    for (int k = 0; k < R; k++) {
+      q = fmaxf(q, cvg_all[k]);
+      o = fmaxf(o, cvg_own[k]);
+    }
+    __syncthreads();
+    own = o;
+    return q;
+  };
+  // verdict on the last speculative unit (slot published by a cluster barrier)
+  auto verified = [&](int vs, float kc0) -> bool {
+    group_ratios<R, grouped>(ver + vs * SL, CL, cphys, true, kc0, ver_all, nullptr);
+    __syncthreads();
+    float q = 0.f;
+    for (int k = 0; k < R; k++) q = fmaxf(q, ver_all[k]);
+    return q <= kRefineTol1;
+  };
   float2 g[H], xh[H];
   int cur_series = -1;
+  int cur_c = -1;
   int parity = 0;
-  int preloaded_item = -1;  // the item whose F g holds (loaded during the previous output)
-  int next_main = cluster_id;
-  int pending = -1;         // a speculative item that failed its verification
-  int unverified = -1;      // the last speculative item, its maxima not checked yet
+  int preloaded = -1;       // the unit whose F g holds (loaded during the previous output)
+  int u_next = grouped ? L.ustart[cluster_id] : cluster_id;
+  const int u_end = grouped ? L.ustart[cluster_id + 1] : L.nitems;
+  const int u_step = grouped ? 1 : nclusters;
+  int pending = -1;         // a speculative unit that failed its verification
+  int unverified = -1;      // the last speculative unit, its maxima not checked yet
   int vslot = 0;            // and its verification slot
-  int nspec = 0;            // speculative items so far (slot rotation)
+  int nspec = 0;            // speculative units so far (slot rotation)
   while (true) {
-    int it;
+    int u;
     bool retry = false;
     if (pending >= 0) {
-      it = pending;
+      u = pending;
       pending = -1;
       retry = true;
-    } else if (next_main < L.nitems) {
-      it = next_main;
-      next_main += nclusters;
-    } else if (unverified >= 0) {   // the last speculative item: check it now
+    } else if (u_next < u_end) {
+      u = u_next;
+      u_next += u_step;
+    } else if (unverified >= 0) {   // the last speculative unit: check it now
       cluster_barrier();
-      verify_columns<R>(ver + vslot * 2 * R, L.C, ver_scratch);
-      __syncthreads();
-      float q = 0.f;
-      for (int k = 0; k < R; k++) q = fmaxf(q, ver_scratch[k]);
-      if (!(q * ITEMX(unverified, contraction) <= kRefineTol1)) pending = unverified;
+      if (!verified(vslot, ITEMX(item_of(unverified), contraction))) pending = unverified;
       unverified = -1;
       __syncthreads();
       continue;
     } else {
       break;
     }
-    // fields of the current item, read where they are used (kernel parameter
-    // or work list; no address of the parameter is taken)
-#define ITEM(fld) ITEMX(it, fld)
-    const int tile = L.single ? it : L.items[it].tile;
-    const int M = ITEM(M);
-    if (ITEM(series) != cur_series) {   // new series: ratios, products, coefficient rows
+    // fields of the current item, read where they are used: kernel parameters
+    // of a single-series launch, else a copy in shared memory (cheap to read
+    // again after every barrier instead of held in registers through the tile)
+    const int it = item_of(u);
+    if constexpr (LM != kLaunchSingle) {
+      __syncthreads();   // every read of the previous item's copy is done
+      if (tid < (int)(sizeof(RefItem) / 4))
+        reinterpret_cast<int*>(&s_item)[tid] = __ldg(reinterpret_cast<const int*>(L.items + it) + tid);
       __syncthreads();
-      iface_df_setup(f, ITEM(rR), ITEM(rL), M, m, L.C, c);
+    }
+#define ITEM(fld) (LM == kLaunchSingle ? L.one.fld : s_item.fld)
+    // pointers and strides read again at every use (from the copy), so that no
+    // address is held in registers through the tile
+#define ITEMV(fld) (LM == kLaunchSingle ? L.one.fld : *(volatile decltype(s_item.fld)*)&s_item.fld)
+    const int gs = grouped ? ITEM(g) : CL;   // CTAs of the group
+    const int m = LM == kLaunchSingle ? L.m : ITEM(m);   // blocks per CTA
+    const unsigned base = group_base(gs);    // the group's first rank
+    const unsigned c = cphys - base;         // rank in the group
+    const int tile = LM == kLaunchSingle ? u : ITEM(tile);
+    const int M = ITEM(M);
+    // new series or new place in the group: ratios, products, coefficient
+    // rows (a null item, M = 0, needs none: its threads have no rows)
+    if (M > 0 && (ITEM(series) != cur_series || (int)c != cur_c)) {
+      __syncthreads();
+      iface_df_setup(f, ITEM(rR), ITEM(rL), M, m, gs, c);
       if constexpr (SM) {   // this CTA's blocks of the table; blocks past M as zeros
         const float4* src = reinterpret_cast<const float4*>(ITEM(tab) + (size_t)c * m * STR);
         float4* dst = reinterpret_cast<float4*>(stab);
@@ -548,10 +611,13 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       }
       __syncthreads();
       cur_series = ITEM(series);
+      cur_c = (int)c;
     }
     const int n = ITEM(n);
     const int b = (int)c * m + bl;
     const bool blk_ok = (bl < m) && (b < M);
+    const bool has_left = blk_ok && b >= 1;          // separators p_b, p_{b+1} inside the matrix
+    const bool has_right = blk_ok && b + 1 <= M - 1;
     const int64_t row0 = (int64_t)b * TT;
     const int nrows = blk_ok ? (int)((n - row0) < TT ? (n - row0) : TT) : 0;
     const int64_t col = (int64_t)tile * R + r;
@@ -559,15 +625,25 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
     const bool active = nrows > 0 && col_ok;   // this thread's rows and column exist
     const float* cb = SM ? stab + (size_t)bl * STR : ITEM(tab) + (size_t)(blk_ok ? b : M) * STR;
     // this thread's rows of F (none for padding threads and missing columns)
-    const Rows<const float> fr{ITEM(F) + row0 * ITEM(ldF) + col, (int)ITEM(ldF), active ? nrows : 0};
+    auto rows_F = [&]() {
+      return Rows<const float>{ITEMV(F) + row0 * ITEMV(ldF) + col, (int)ITEMV(ldF), active ? nrows : 0};
+    };
     const int steps_cfg = ITEM(steps);
-    const int mode = retry ? kRetry
-                           : steps_cfg == kRefineCalib ? kCalib
-                           : steps_cfg == -1 ? (ITEM(contraction) < 1.f ? kSpec : kTested) : kFixed;
-    const bool track = mode == kTested || mode == kRetry || mode == kCalib;
-    const int cap = mode == kFixed ? steps_cfg : mode == kSpec ? 1 : mode == kCalib ? kRefineCalibSteps : kRefineCap;
+#define KC ITEM(contraction)
+    int mode;
+    if (grouped)
+      mode = retry ? kRetryFixed : steps_cfg == -1 ? (KC < 1.f ? kSpec : kRetryFixed) : kFixed;
+    else
+      mode = retry ? kRetry
+                   : steps_cfg == kRefineCalib ? kCalib
+                   : steps_cfg == -1 ? (KC < 1.f ? kSpec : kTested) : kFixed;
+    const bool intest = mode == kTested || mode == kRetry || mode == kCalib;   // tests between corrections
+    const bool track = intest || mode == kRetryFixed;                          // corrections' maxima kept
+    const int cap = mode == kFixed ? steps_cfg
+                  : mode == kSpec ? 1
+                  : mode == kCalib ? kRefineCalibSteps : kRefineCap;
 
-    if (preloaded_item != it) load_rhs<TT>(g, fr);
+    if (preloaded != u) load_rhs<TT>(g, rows_F());
 
     // ---- first solve (A2-A5): x = (xh, xl) ------------------------------------
     float maxx = 0.f;
@@ -581,42 +657,47 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       cluster_arrive();   // the back substitution overlaps the exchange of the CTA totals
       backward_y<TT, SM>(g, cb);
       cluster_wait();
-      iface_df_fold<R, MM, true, true>(f, L.C, c, parity);
-      // the exchange also published the last speculative tile's maxima
-      if (unverified >= 0) verify_columns<R>(ver + vslot * 2 * R, L.C, ver_scratch);
-      __syncthreads();
-      parity ^= 1;
-      if (unverified >= 0) {   // every CTA reaches the same verdict from the same maxima
-        float q = 0.f;
-        for (int k = 0; k < R; k++) q = fmaxf(q, ver_scratch[k]);
-        if (!(q * ITEMX(unverified, contraction) <= kRefineTol1)) pending = unverified;
+      iface_df_fold<R, MM, true, true>(f, gs, c, parity, base);
+      // the exchange also published the last speculative unit's maxima; every
+      // CTA reaches the same verdict from the same maxima
+      if (unverified >= 0) {
+        if (!verified(vslot, ITEMX(item_of(unverified), contraction))) pending = unverified;
         unverified = -1;
+      } else {
+        __syncthreads();
       }
+      parity ^= 1;
       f2pair xL{0.f, 0.f}, xR{0.f, 0.f};
-      if (blk_ok) {
-        if (b >= 1) xL = iface_df_sep_pair<R, MM, true, true>(f, bl, r);
-        if (b + 1 <= M - 1) xR = iface_df_sep_pair<R, MM, true, true>(f, bl + 1, r);
-      }
-      first_correction<TT, SM>(g, xh, xlp, cb, xL, xR, fr, maxx);
+      if (has_left) xL = iface_df_sep_pair<R, MM, true, true>(f, bl, r);
+      if (has_right) xR = iface_df_sep_pair<R, MM, true, true>(f, bl + 1, r);
+      first_correction<TT, SM>(g, xh, xlp, cb, xL, xR, rows_F(), maxx);
     }
     if (!col_ok) maxx = 0.f;
 
     // ---- corrections: r = F - A x, d = solve(r), x += d ----------------------
-    const int64_t ldX = ITEM(ldX);
-    const Rows<double> xr{ITEM(X) + row0 * ldX + col, (int)ldX, active ? nrows : 0};
-    // the item that runs next, whose F the output loads
-    const int nxt = pending >= 0 ? pending : (next_main < L.nitems ? next_main : -1);
-    Rows<const float> fn{ITEM(F), 0, 0};
-    if (nxt >= 0) {
-      const int tile_n = L.single ? nxt : L.items[nxt].tile;
-      const int64_t col_n = (int64_t)tile_n * R + r;
-      const int n_n = ITEMX(nxt, n);
-      if ((bl < m) && (b < ITEMX(nxt, M)) && col_n < ITEMX(nxt, N)) {
-        fn.rows = (int)((n_n - row0) < TT ? (n_n - row0) : TT);
-        fn.ld32 = (int)ITEMX(nxt, ldF);
-        fn.base = ITEMX(nxt, F) + row0 * ITEMX(nxt, ldF) + col_n;
+    auto rows_X = [&]() {
+      return Rows<double>{ITEMV(X) + row0 * ITEMV(ldX) + col, (int)ITEMV(ldX), active ? nrows : 0};
+    };
+    // the unit that runs next, whose F (in its own item's rows) the output loads
+    const int nu = pending >= 0 ? pending : (u_next < u_end ? u_next : -1);
+    auto rows_next = [&]() {
+      Rows<const float> fn{ITEMV(F), 0, 0};
+      if (nu >= 0) {
+        const int itn = item_of(nu);
+        const int gn = grouped ? ITEMX(itn, g) : CL, mn = LM == kLaunchSingle ? L.m : ITEMX(itn, m);
+        const int bn = (int)(cphys - group_base(gn)) * mn + bl;
+        const int tile_n = LM == kLaunchSingle ? nu : L.items[itn].tile;
+        const int64_t col_n = (int64_t)tile_n * R + r;
+        const int64_t row0_n = (int64_t)bn * TT;
+        const int n_n = ITEMX(itn, n);
+        if (bl < mn && bn < ITEMX(itn, M) && col_n < ITEMX(itn, N)) {
+          fn.rows = (int)((n_n - row0_n) < TT ? (n_n - row0_n) : TT);
+          fn.ld32 = (int)ITEMX(itn, ldF);
+          fn.base = ITEMX(itn, F) + row0_n * ITEMX(itn, ldF) + col_n;
+        }
       }
-    }
+      return fn;
+    };
     float ratio_prev = 1.f;
     int done = 0;
     bool fused_out = false;
@@ -630,14 +711,14 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       // Tests read every CTA's maxima of the last correction: a full cluster
       // barrier, which also publishes the edge values.  Otherwise the interior
       // of the residual overlaps the edge-value barrier.
-      const bool test = track && done >= (mode == kRetry ? 2 : 1);
+      const bool test = intest && done >= (mode == kRetry ? 2 : 1);
       if (test) {
         cluster_barrier();
-        const float ratio = cluster_ratio<R>(cvg + (done & 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
+        float own;
+        const float ratio = ratios(cvg + (done & 1) * SL, own);
         if (mode == kCalib && tid == 0 && c == 0) atomicMax(&g_tdm_calib[done - 1], __float_as_uint(ratio));
         if (mode != kCalib) {
-          const bool stop = done == 1 ? ratio * ITEM(contraction) <= kRefineTol1
-                                      : ratio * ratio <= kRefineTol * ratio_prev;
+          const bool stop = done == 1 ? ratio * KC <= kRefineTol1 : ratio * ratio <= kRefineTol * ratio_prev;
           if (stop) break;
         }
         ratio_prev = ratio;
@@ -649,18 +730,21 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       df2 E0, Elast;
       residual_interior<TT, SM>(g, xh, xlp, cb, E0, Elast);
       if (!test) cluster_wait();
-      if (mode == kRetry && done == 1)
-        ratio_prev = cluster_ratio<R>(cvg + (done & 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
+      if (mode == kRetry && done == 1) {
+        float own;
+        ratio_prev = ratios(cvg + (done & 1) * SL, own);
+      }
       f2pair xm{0.f, 0.f}, xp{0.f, 0.f};   // x at rows row0-1 and row0+TT
       if (bl > 0) {
         xm = f2pair{eLh[(bl - 1) * R + r], eLl[(bl - 1) * R + r]};
       } else if (c > 0) {
-        xm = f2pair{ld_cluster_f32(eLh + (m - 1) * R + r, c - 1), ld_cluster_f32(eLl + (m - 1) * R + r, c - 1)};
+        xm = f2pair{ld_cluster_f32(eLh + (m - 1) * R + r, base + c - 1),
+                    ld_cluster_f32(eLl + (m - 1) * R + r, base + c - 1)};
       }
       if (bl < m - 1) {
         xp = f2pair{eFh[(bl + 1) * R + r], eFl[(bl + 1) * R + r]};
-      } else if ((int)c < L.C - 1) {
-        xp = f2pair{ld_cluster_f32(eFh + r, c + 1), ld_cluster_f32(eFl + r, c + 1)};
+      } else if ((int)c < gs - 1) {
+        xp = f2pair{ld_cluster_f32(eFh + r, base + c + 1), ld_cluster_f32(eFl + r, base + c + 1)};
       }
       residual_edges<TT, SM>(g, xh, xlp, cb, xm, xp, E0, Elast);
 
@@ -674,20 +758,18 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       cluster_arrive();
       backward_y<TT, SM>(g, cb);
       cluster_wait();
-      iface_df_fold<R, MM, true, false>(f, L.C, c, parity);
+      iface_df_fold<R, MM, true, false>(f, gs, c, parity, base);
       __syncthreads();
       parity ^= 1;
       float xL = 0.f, xR = 0.f;
-      if (blk_ok) {
-        if (b >= 1) xL = iface_df_sep_pair<R, MM, true, false>(f, bl, r).h;
-        if (b + 1 <= M - 1) xR = iface_df_sep_pair<R, MM, true, false>(f, bl + 1, r).h;
-      }
+      if (has_left) xL = iface_df_sep_pair<R, MM, true, false>(f, bl, r).h;
+      if (has_right) xR = iface_df_sep_pair<R, MM, true, false>(f, bl + 1, r).h;
       done++;
       if (!track && done == cap) {   // the last correction is added in the output
         float maxd = 0.f;
-        output<TT, SM, true>(g, xh, xlp, cb, xL, xR, xr, fn, maxd);
+        output<TT, SM, true>(g, xh, xlp, cb, xL, xR, rows_X(), rows_next(), maxd);
         fused_out = true;
-        if (mode == kSpec) {   // this CTA's per-column maxima into the tile's verification slot
+        if (mode == kSpec) {   // this CTA's per-column maxima into the unit's verification slot
           const int slot = nspec % kVerSlots;
           if (!col_ok) maxd = 0.f;
           float md = maxd, mx = maxx;
@@ -697,38 +779,60 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
             mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
           }
           if ((tid & 31) < R) {
-            atomicMax(reinterpret_cast<unsigned*>(ver) + (slot * 2 + 0) * R + r, __float_as_uint(md));
-            atomicMax(reinterpret_cast<unsigned*>(ver) + (slot * 2 + 1) * R + r, __float_as_uint(mx));
+            atomicMax(reinterpret_cast<unsigned*>(ver) + slot * SL + r, __float_as_uint(md));
+            atomicMax(reinterpret_cast<unsigned*>(ver) + slot * SL + R + r, __float_as_uint(mx));
           }
-          // the slot two speculative tiles ahead: its last readers have passed
+          if (tid == 0) {
+            ver[slot * SL + 2 * R] = (float)gs;
+            ver[slot * SL + 2 * R + 1] = KC;
+          }
+          // the slot two speculative units ahead: its last readers have passed
           // at least one cluster barrier since
           const int z = (nspec + 2) % kVerSlots;
-          if (tid < 2 * R) ver[z * 2 * R + tid] = 0.f;
-          unverified = it;
+          if (tid < SL) ver[z * SL + tid] = 0.f;
+          unverified = u;
           vslot = slot;
           nspec++;
         }
         break;
       }
       float maxd = 0.f;
-      if (done < cap) correction_update<TT, SM, true>(g, xh, xlp, cb, xL, xR, maxd, fr);
-      else correction_update<TT, SM, false>(g, xh, xlp, cb, xL, xR, maxd, fr);
-      if (track) {
+      if (done < cap) correction_update<TT, SM, true>(g, xh, xlp, cb, xL, xR, maxd, rows_F());
+      else correction_update<TT, SM, false>(g, xh, xlp, cb, xL, xR, maxd, rows_F());
+      if (track) {   // tested modes alternate two slots; the fixed retry keeps one per correction
         if (!col_ok) maxd = 0.f;   // padding columns of a ragged tile do not vote
-        cta_maxima<R>(maxd, maxx, red, cvg + (done & 1) * 2 * R, tid);
+        cta_maxima<R>(maxd, maxx, red, cvg + (intest ? (done & 1) : (done - 1) & 3) * SL, tid, gs, KC);
       }
     }
     if (!fused_out) {
       if (track && done == cap) {   // cap reached: record the last correction
         cluster_barrier();
-        const float ratio = cluster_ratio<R>(cvg + (done & 1) * 2 * R, L.C, tid, cvg_scratch, &ratio_s);
-        if (mode == kCalib && tid == 0 && c == 0) atomicMax(&g_tdm_calib[done - 1], __float_as_uint(ratio));
-        if (mode != kCalib && tid == 0 && !(ratio * ratio <= kRefineTol * ratio_prev)) atomicExch(L.err, kDevErrNotConverged);
+        if (mode == kRetryFixed) {   // per group: would the tested criterion have stopped by now?
+          float prev, cur;
+          ratios(cvg, prev);
+          bool conv = false;
+          for (int k = 2; k <= cap; k++) {
+            ratios(cvg + (k - 1) * SL, cur);
+            conv = conv || cur * cur <= kRefineTol * prev;
+            prev = cur;
+          }
+          if (tid == 0 && c == 0 && !conv) atomicExch(L.err, kDevErrNotConverged);
+        } else {
+          float own;
+          const float ratio = ratios(cvg + (done & 1) * SL, own);
+          if (mode == kCalib) {
+            if (tid == 0 && c == 0) atomicMax(&g_tdm_calib[done - 1], __float_as_uint(ratio));
+          } else if (tid == 0 && !(ratio * ratio <= kRefineTol * ratio_prev)) {
+            atomicExch(L.err, kDevErrNotConverged);
+          }
+        }
       }
       float unused = 0.f;
-      output<TT, SM, false>(g, xh, xlp, cb, 0.f, 0.f, xr, fn, unused);
+      output<TT, SM, false>(g, xh, xlp, cb, 0.f, 0.f, rows_X(), rows_next(), unused);
     }
-    preloaded_item = nxt;
+    preloaded = nu;
+#undef KC
+#undef ITEMV
 #undef ITEM
   }
 #undef ITEMX
@@ -736,17 +840,22 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   cluster_barrier();
 }
 
-template <int R, int TT, int NT, int MINB, bool SM>
-tdm_status launch_shape(const RefShape& sh, const RefLaunch& L, int nitems, cudaStream_t s) {
-  auto kern = k_refined<R, TT, NT, MINB, SM>;
-  static std::mutex mu;
-  static std::map<std::tuple<int, int, size_t, int>, int> occ;   // (device, C, smem, threads) -> clusters
-  int dev = 0;
-  cudaGetDevice(&dev);
+template <int R_, int TT_, int NT_, int MINB_, bool SM_>
+struct ShapeTag {
+  static constexpr int R = R_, TT = TT_, NT = NT_, MINB = MINB_;
+  static constexpr bool SM = SM_;
+};
+// the kernel of a shape: grouped launches, or single-series and list launches
+template <class S, int LM>
+constexpr auto refined_kernel() { return k_refined<S::R, S::TT, S::NT, S::MINB, S::SM, LM>; }
+
+// launch configuration of a shape's kernel (grid filled in by the caller)
+template <class S, int G>
+tdm_status shape_config(const RefShape& sh, cudaStream_t s, cudaLaunchConfig_t& lc, cudaLaunchAttribute* at) {
+  auto kern = refined_kernel<S, G>();
   TDM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem));
   if (sh.C > 8) TDM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  cudaLaunchConfig_t lc = {};
-  cudaLaunchAttribute at[1];
+  lc = cudaLaunchConfig_t{};
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = sh.C;
   at[0].val.clusterDim.y = 1;
@@ -756,26 +865,60 @@ tdm_status launch_shape(const RefShape& sh, const RefLaunch& L, int nitems, cuda
   lc.stream = s;
   lc.attrs = at;
   lc.numAttrs = 1;
-  int maxc = 0;
-  {
-    std::lock_guard<std::mutex> g(mu);
-    auto key = std::make_tuple(dev, sh.C, sh.smem, sh.threads);
-    auto it = occ.find(key);
-    if (it != occ.end()) {
-      maxc = it->second;
-    } else {
-      lc.gridDim = dim3(sh.C);
-      if (cudaOccupancyMaxActiveClusters(&maxc, (void*)kern, &lc) != cudaSuccess || maxc < 1) {
-        (void)cudaGetLastError();
-        maxc = 1;
-      }
-      occ[key] = maxc;
-    }
-  }
-  const int nclusters = nitems < maxc ? nitems : maxc;
-  lc.gridDim = dim3(nclusters * sh.C);
-  TDM_CUDA_TRY(cudaLaunchKernelEx(&lc, kern, L));
   return TDM_OK;
+}
+
+// clusters of the shape that the device holds at once (cached per device,
+// cluster size, shared memory and block size)
+template <class S, int G>
+int shape_max_clusters(const RefShape& sh) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, size_t, int>, int> occ;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_tuple(dev, sh.C, sh.smem, sh.threads);
+  auto it = occ.find(key);
+  if (it != occ.end()) return it->second;
+  cudaLaunchConfig_t lc;
+  cudaLaunchAttribute at[1];
+  int maxc = 0;
+  if (shape_config<S, G>(sh, 0, lc, at) != TDM_OK) maxc = 1;
+  lc.gridDim = dim3(sh.C);
+  if (maxc == 0 && (cudaOccupancyMaxActiveClusters(&maxc, (void*)refined_kernel<S, G>(), &lc) != cudaSuccess ||
+                    maxc < 1)) {
+    (void)cudaGetLastError();
+    maxc = 1;
+  }
+  occ[key] = maxc;
+  return maxc;
+}
+
+template <class S, int G>
+tdm_status launch_shape(const RefShape& sh, const RefLaunch& L, int nclusters, cudaStream_t s) {
+  cudaLaunchConfig_t lc;
+  cudaLaunchAttribute at[1];
+  tdm_status st = shape_config<S, G>(sh, s, lc, at);
+  if (st != TDM_OK) return st;
+  lc.gridDim = dim3(nclusters * sh.C);
+  TDM_CUDA_TRY(cudaLaunchKernelEx(&lc, refined_kernel<S, G>(), L));
+  return TDM_OK;
+}
+
+// calls fn(ShapeTag<...>{}) for the kernel of a shape, false if none
+template <class Fn>
+bool with_shape(const RefShape& sh, int t, Fn&& fn) {
+  const int key = sh.R * 100000 + sh.NT * 10 + (t == 16 ? 1 : 0);
+  switch (key) {
+    case 8 * 100000 + 256 * 10 + 0: fn(ShapeTag<8, 32, 256, 2, true>{}); return true;
+    case 8 * 100000 + 512 * 10 + 0: fn(ShapeTag<8, 32, 512, 1, true>{}); return true;
+    case 4 * 100000 + 512 * 10 + 0: fn(ShapeTag<4, 32, 512, 1, false>{}); return true;
+    case 16 * 100000 + 512 * 10 + 0: fn(ShapeTag<16, 32, 512, 1, true>{}); return true;
+    case 8 * 100000 + 256 * 10 + 1: fn(ShapeTag<8, 16, 256, 2, true>{}); return true;
+    case 8 * 100000 + 512 * 10 + 1: fn(ShapeTag<8, 16, 512, 1, true>{}); return true;
+    case 4 * 100000 + 1024 * 10 + 1: fn(ShapeTag<4, 16, 1024, 1, false>{}); return true;
+  }
+  return false;
 }
 
 struct RefCand {
@@ -829,29 +972,57 @@ tdm_status tdm_refined_launch(const RefShape& sh, int t, const RefItem* items, c
   RefLaunch L;
   memset(&L, 0, sizeof(L));
   L.items = items;
-  if (one) L.one = *one;
+  if (one) {
+    L.one = *one;
+    L.one.m = sh.m;
+    L.one.g = sh.C;
+  }
   L.nitems = nitems;
   L.single = items ? 0 : 1;
   L.m = sh.m;
   L.C = sh.C;
   L.err = err;
-  const int key = sh.R * 100000 + sh.NT * 10 + (t == 16 ? 1 : 0);
-  switch (key) {
-    case 8 * 100000 + 256 * 10 + 0: return launch_shape<8, 32, 256, 2, true>(sh, L, nitems, s);
-    case 8 * 100000 + 512 * 10 + 0: return launch_shape<8, 32, 512, 1, true>(sh, L, nitems, s);
-    case 4 * 100000 + 512 * 10 + 0: return launch_shape<4, 32, 512, 1, false>(sh, L, nitems, s);
-    case 16 * 100000 + 512 * 10 + 0: return launch_shape<16, 32, 512, 1, true>(sh, L, nitems, s);
-    case 8 * 100000 + 256 * 10 + 1: return launch_shape<8, 16, 256, 2, true>(sh, L, nitems, s);
-    case 8 * 100000 + 512 * 10 + 1: return launch_shape<8, 16, 512, 1, true>(sh, L, nitems, s);
-    case 4 * 100000 + 1024 * 10 + 1: return launch_shape<4, 16, 1024, 1, false>(sh, L, nitems, s);
-  }
-  return TDM_ERR_NOT_IMPLEMENTED;
+  tdm_status st = TDM_OK;
+  if (!with_shape(sh, t, [&](auto tag) {
+        using S = decltype(tag);
+        const int maxc = shape_max_clusters<S, kLaunchSingle>(sh);
+        if (items) st = launch_shape<S, kLaunchList>(sh, L, nitems < maxc ? nitems : maxc, s);
+        else st = launch_shape<S, kLaunchSingle>(sh, L, nitems < maxc ? nitems : maxc, s);
+      }))
+    return TDM_ERR_NOT_IMPLEMENTED;
+  return st;
+}
+
+tdm_status tdm_refined_launch_grouped(const RefShape& sh, int t, const RefItem* items, const int* units,
+                                      const int* ustart, int nclusters, int* err, cudaStream_t s) {
+  if (nclusters <= 0) return TDM_OK;
+  RefLaunch L;
+  memset(&L, 0, sizeof(L));
+  L.items = items;
+  L.units = units;
+  L.ustart = ustart;
+  L.single = 0;
+  L.m = sh.m;
+  L.C = sh.C;
+  L.err = err;
+  tdm_status st = TDM_OK;
+  if (!with_shape(sh, t, [&](auto tag) { st = launch_shape<decltype(tag), kLaunchGrouped>(sh, L, nclusters, s); }))
+    return TDM_ERR_NOT_IMPLEMENTED;
+  return st;
+}
+
+int tdm_refined_max_clusters(const RefShape& sh, int t) {
+  int maxc = 0;
+  if (!with_shape(sh, t, [&](auto tag) { maxc = shape_max_clusters<decltype(tag), kLaunchGrouped>(sh); })) return 0;
+  return maxc;
 }
 
 RefItem tdm_refined_item(const tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX, int64_t N,
-                         int series) {
+                         int series, const RefShape& sh) {
   RefItem it;
   memset(&it, 0, sizeof(it));
+  it.m = sh.m;
+  it.g = sh.C;
   it.F = F; it.X = X; it.ldF = ldF; it.ldX = ldX;
   it.tab = p->rtab; it.rR = p->rR; it.rL = p->rL;
   it.n = (int)p->n; it.M = p->M; it.N = (int)N; it.tile = 0;
@@ -866,7 +1037,7 @@ tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double
   if (ldF > kRefMaxLd || ldX > kRefMaxLd) return TDM_ERR_NOT_IMPLEMENTED;
   RefShape sh;
   if (!tdm_refined_shape(p->M, p->t, p->tile_rhs, sh)) return TDM_ERR_NOT_IMPLEMENTED;
-  const RefItem one = tdm_refined_item(p, F, ldF, X, ldX, N, 0);
+  const RefItem one = tdm_refined_item(p, F, ldF, X, ldX, N, 0, sh);
   const int ntiles = (int)((N + sh.R - 1) / sh.R);
   return tdm_refined_launch(sh, p->t, nullptr, &one, ntiles, p->dev_err, s);
 }

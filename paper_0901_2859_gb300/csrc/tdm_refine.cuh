@@ -40,7 +40,7 @@ struct RefItem {
   double* X;
   int64_t ldF, ldX;
   const float* tab;    // [M + 1][kRefTabStride(t)] coefficient table
-  const void* spare;   // unused (keeps the item at 96 bytes)
+  int m, g;            // blocks per CTA, CTAs of the group that solves the tile
   const double* rR;
   const double* rL;
   int n, M, N, tile;
@@ -50,12 +50,21 @@ struct RefItem {
   int pad1;
 };
 
+// Grouped launches: a unit is one step of a cluster, in which every CTA works
+// on the item units[u * kUnitW + rank] (a null item when it has nothing to
+// do).  An item of group size g occupies the g CTAs of an aligned range
+// (rank & ~(g - 1) .. + g - 1); g is a power of two.  Cluster k walks units
+// ustart[k] .. ustart[k + 1] - 1 in order.
+constexpr int kUnitW = 16;
+
 struct RefLaunch {
   const RefItem* items;   // work list (device); unused when single
+  const int* units;       // grouped: [units][kUnitW] item of every CTA; null otherwise
+  const int* ustart;      // grouped: [clusters + 1] first unit of every cluster
   RefItem one;            // the series of a single-series launch (item i = its tile i)
-  int nitems;
+  int nitems;             // single: tiles; list: items (cluster k takes k, k + clusters, ...)
   int single;
-  int m, C;               // blocks per CTA, CTAs per cluster
+  int m, C;               // single: blocks per CTA; CTAs per cluster
   int* err;
 };
 
@@ -77,11 +86,22 @@ constexpr int kRefineCalibSteps = 4;
 
 // pref: requested right-hand sides per tile (0 = by the rule)
 bool tdm_refined_shape(int M, int t, int pref, RefShape& sh);
-// enqueue one launch over `nitems` items (items == nullptr: single series `one`)
+// enqueue one launch over `nitems` items (items == nullptr: single series `one`); every CTA of a
+// cluster works on the same item (g = sh.C; list items carry their own m <= NT / R)
 tdm_status tdm_refined_launch(const RefShape& sh, int t, const RefItem* items, const RefItem* one,
                               int nitems, int* err, cudaStream_t s);
+// enqueue a grouped launch: `nclusters` clusters of sh.C CTAs walk the unit
+// lists (sh.m is not used: every item carries its own m and g)
+tdm_status tdm_refined_launch_grouped(const RefShape& sh, int t, const RefItem* items, const int* units,
+                                      const int* ustart, int nclusters, int* err, cudaStream_t s);
+// clusters of sh.C CTAs of the shape's kernel that the device holds at once
+int tdm_refined_max_clusters(const RefShape& sh, int t);
+// the refined solve of one series (one single-series launch)
+tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX, int64_t N,
+                              cudaStream_t s);
 // the calibration record: max over tiles of max|d_k| / max|x| for corrections
 // k = 1 .. kRefineCalibSteps of calibration solves (cleared, or read into ratios)
 tdm_status tdm_calibration_record(bool clear, float* ratios, cudaStream_t s);
+// an item of series p in tile shape sh (every CTA of the cluster on it: m = sh.m, g = sh.C)
 RefItem tdm_refined_item(const tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX,
-                         int64_t N, int series);
+                         int64_t N, int series, const RefShape& sh);

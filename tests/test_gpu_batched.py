@@ -110,3 +110,128 @@ def test_batched_other_precisions(tdm, dev, oracle, precision):
         assert relerr(xb.cpu().numpy(), ref) <= (1e-11 if precision == "fp64" else 2e-5)
     for p in plans:
         p.close()
+
+
+@pytest.fixture
+def grouped(tdm):
+    tdm.set_batched_strategy("grouped")
+    yield
+    tdm.set_batched_strategy("auto")
+
+
+@pytest.mark.parametrize("strategy", ["per_series", "by_width", "grouped"])
+def test_batched_strategies_match_single_solves(tdm, dev, oracle, strategy):
+    """Both layouts of the batched work give every series the result of its own
+    solve, bit for bit, over sizes that need clusters of 1 to 16 CTAs and
+    three kernel shapes (up to n = 40000)."""
+    sizes = [(300, 9), (700, 30), (2100, 17), (5000, 8), (9000, 21), (15000, 5), (20000, 6), (40000, 3)]
+    from paper_0901_2859_gb300 import workloads
+    series = []
+    for m, (n, N) in enumerate(sizes):
+        rng = np.random.default_rng(40 + m)
+        s = 4.0 * np.sin(np.pi * (m + 1) / (2.0 * 65)) ** 2
+        series.append(workloads.Series(-np.ones(n - 1), np.full(n, 2.0 + s),
+                                       rng.standard_normal((n, N), dtype=np.float32)))
+    plans, Fs = _upload(tdm, dev, series)
+    tdm.set_batched_strategy(strategy)
+    try:
+        Xb = tdm.solve_batched(plans, Fs, "fp32_refined")
+    finally:
+        tdm.set_batched_strategy("auto")
+    Xs = [p.solve(F, "fp32_refined") for p, F in zip(plans, Fs)]
+    torch.cuda.synchronize()
+    for s, xb, xs in zip(series, Xb, Xs):
+        assert torch.equal(xb, xs), s.n
+    ref = oracle.solve_hi(series[4].a, series[4].b, series[4].F.astype(np.float64))
+    assert relerr(Xb[4].cpu().numpy(), ref) <= 1e-11
+    for p in plans:
+        assert p.info()["device_error"] == 0
+        p.close()
+
+
+def test_grouped_launch_mixed_schedules(tdm, dev, oracle, grouped):
+    """Plans of three correction schedules in one call -- the calibrated
+    per-tile test, two fixed corrections, the uncalibrated test -- each in a
+    grouped launch of its own.  The first two equal the plan's own solve bit
+    for bit (a series keeps its single-series partition inside its group); the
+    third runs the fixed retry count; all meet the gate."""
+    series = _batch(seed=5, count=18, n_min=100, n_max=9000, N_max=50)
+    steps = [0, 2, -1] * 6
+    plans = [tdm.prepare(s.a, s.b, refine_steps=k, device=dev) for s, k in zip(series, steps)]
+    Fs = [torch.from_numpy(s.F).to(dev) for s in series]
+    Xb = tdm.solve_batched(plans, Fs, "fp32_refined")
+    Xs = [p.solve(F, "fp32_refined") for p, F in zip(plans, Fs)]
+    torch.cuda.synchronize()
+    for s, k, xb, xs in zip(series, steps, Xb, Xs):
+        if k != -1:
+            assert torch.equal(xb, xs), (s.n, k)
+        ref = oracle.solve_hi(s.a, s.b, s.F.astype(np.float64))
+        assert relerr(xb.cpu().numpy(), ref) <= 1e-11, (s.n, k)
+    for p in plans:
+        assert p.info()["device_error"] == 0
+        p.close()
+
+
+def test_grouped_launch_retries_a_failing_unit(tdm, dev, oracle, grouped):
+    """Pure high sine modes at kappa ~ 3.4e6 (n = 4096, a group of 4 CTAs) need
+    more than one correction: the speculative test fails on their units, and
+    the cluster solves each such unit again with the fixed retry count --
+    together with the tiles of the other series that shared the unit (a
+    16-CTA series sets the cluster width, 1-CTA series fill the gaps).
+    Everything meets its gate and no tile reports non-convergence."""
+    from paper_0901_2859_gb300 import workloads
+    s4 = workloads.poisson2d(seed=1)
+    n = s4.n
+    ks = [n // 2, n - 1, n] * 6
+    Fe, _, lam = oracle.eigen_closed_form(n, s4.b[0], ks)
+    lam_min = oracle.eigen_closed_form(n, s4.b[0], [1])[2][0]
+    series = [workloads.Series(s4.a, s4.b, Fe.astype(np.float32))]
+    tols = [[max(1e-11, 0.1 * 2.0 ** -48 * np.sqrt(lam[c]) / lam_min) for c in range(len(ks))]]
+    big = workloads.precision(seed=2, n=16384, N=24, s=1e-6)
+    series.append(big)
+    tols.append([1e-11] * big.F.shape[1])
+    for m in range(10):
+        rng = np.random.default_rng(100 + m)
+        nn = int(rng.integers(200, 1000))
+        sh = 4.0 * np.sin(np.pi * (m + 1) / (2.0 * 513)) ** 2
+        series.append(workloads.Series(-np.ones(nn - 1), np.full(nn, 2.0 + sh),
+                                       rng.standard_normal((nn, 40), dtype=np.float32)))
+        tols.append([1e-11] * 40)
+    plans, Fs = _upload(tdm, dev, series)
+    Xb = tdm.solve_batched(plans, Fs, "fp32_refined")
+    torch.cuda.synchronize()
+    for s, tol, xb in zip(series, tols, Xb):
+        ref = oracle.solve_hi(s.a, s.b, s.F.astype(np.float64))
+        x = xb.cpu().numpy()
+        errs = [relerr(x[:, c], ref[:, c]) for c in range(x.shape[1])]
+        assert all(e <= t for e, t in zip(errs, tol)), (s.n, max(errs))
+    for p in plans:
+        assert p.info()["device_error"] == 0
+        p.close()
+
+
+def test_batching_workload_sampled_against_the_oracle(tdm, dev, oracle):
+    """The full batching workload (512 Fourier-mode matrices of lognormal size
+    up to n = 43943, 1.7e9 unknowns, F ~ N(0,1) drawn on the device) in one
+    call, as the benchmark runs it; sampled columns of 16 matrices (the three
+    largest and 13 others) against the oracle's solve."""
+    from paper_0901_2859_gb300 import workloads
+    specs = workloads.batching(seed=0, rhs=False)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234)
+    plans = [tdm.prepare(s.a, s.b, device=dev) for s in specs]
+    Fs = [torch.randn((s.n, s.meta["N"]), device=dev, dtype=torch.float32, generator=gen) for s in specs]
+    Xs = tdm.solve_batched(plans, Fs, "fp32_refined")
+    torch.cuda.synchronize()
+    order = np.argsort([s.n for s in specs])
+    rng = np.random.default_rng(7)
+    pick = list(order[-3:]) + list(rng.choice(order[:-3], size=13, replace=False))
+    for k in pick:
+        s, N = specs[k], specs[k].meta["N"]
+        cols = np.unique(np.r_[0, N - 1, rng.integers(0, N, size=2)])
+        F = Fs[k][:, cols].cpu().numpy().astype(np.float64)
+        ref = oracle.solve_hi(s.a, s.b, F)
+        assert relerr(Xs[k][:, cols].cpu().numpy(), ref) <= 1e-11, (k, s.n, N)
+    assert all(p.info()["device_error"] == 0 for p in plans)
+    for p in plans:
+        p.close()
