@@ -34,6 +34,11 @@
  *  - Invalid arguments are rejected on the host before any launch with
  *    TDM_ERR_INVALID_ARG; nothing is enqueued in that case.
  *  - Handles are not thread-safe: one host thread at a time per handle.
+ *  - Refined solves of one plan must be ordered on the device (one stream, or
+ *    streams ordered by events): where clusters of the plan's width would
+ *    leave many CTA slots idle (13 to 16 CTAs), the solve is a cooperative
+ *    launch whose CTA groups exchange values through a scratch buffer of the
+ *    plan.
  *  - Solves may be captured into a CUDA graph.  A captured solve is not
  *    tracked by tdm_get_info / tdm_destroy; synchronize the graph's stream
  *    before destroying a plan it uses.  A batched call builds its device work
@@ -113,7 +118,8 @@ typedef struct {
   double min_abs_pivot;    /* smallest |pivot| met in prepare, relative to ||A||_inf */
   int32_t device_error;    /* device-side error code of the last solves (0 = none,
                               1 = a TMA transfer timed out, 2 = refinement cap reached
-                              before the convergence test passed) */
+                              before the convergence test passed, 3 = a CTA of a
+                              cooperative refined launch waited too long for its group) */
   int32_t tile_rhs;        /* the plan's tile_rhs option (0 = automatic) */
   int32_t general;         /* 1 for a plan of tdm_prepare_general (a nonsymmetric matrix) */
   float contraction;       /* TDM_FP32_REFINED per-tile test: estimated relative error left by

@@ -9,7 +9,7 @@
 tdm_status tdm_launch_plain(tdm_plan_s* p, const void* F, int64_t ldF, void* X, int64_t ldX,
                             int64_t N, bool fp64, cudaStream_t s);
 tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX,
-                              int64_t N, cudaStream_t s);
+                              int64_t N, cudaStream_t s, bool allow_coop);
 
 namespace {
 
@@ -140,7 +140,7 @@ tdm_status tdm_launch_solve(tdm_plan_s* p, const void* F, int64_t ldF, void* X, 
     case TDM_FP64: st = tdm_launch_plain(p, F, ldF, X, ldX, N, true, s); break;
     case TDM_FP32: st = tdm_launch_plain(p, F, ldF, X, ldX, N, false, s); break;
     case TDM_FP32_REFINED:
-      st = tdm_launch_refined(p, static_cast<const float*>(F), ldF, static_cast<double*>(X), ldX, N, s);
+      st = tdm_launch_refined(p, static_cast<const float*>(F), ldF, static_cast<double*>(X), ldX, N, s, true);
       break;
   }
   // a plan beyond one cluster: the two-level solve (the direct kernels refuse before launching)

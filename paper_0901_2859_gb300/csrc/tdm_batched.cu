@@ -387,7 +387,7 @@ tdm_status tdm_launch_batched(tdm_plan_s* const* ps, int count, const void* cons
       const int k = ks[i];
       cudaStream_t ls = (i % nstreams) == 0 ? s : hp->st[(i % nstreams) - 1];
       st = tdm_launch_refined(ps[k], static_cast<const float*>(F[k]), ldF[k], static_cast<double*>(X[k]), ldX[k],
-                              N[k], ls);
+                              N[k], ls, false);
     }
     if (hp) {
       for (int i = 0; i < Helpers::kStreams; i++) {

@@ -88,6 +88,7 @@ struct IfaceDF {
   // row keeps both directions free of bank conflicts.
   static constexpr int kRP = R + 1;
   unsigned char* base;
+  float2* xg = nullptr;   // the totals in global memory instead (cooperative launches)
   __device__ float* beR() const { return reinterpret_cast<float*>(base + O.beR); }
   __device__ float* beL() const { return reinterpret_cast<float*>(base + O.beL); }
   // LR_j, LL_j entries: pairs (PAIR) or their leading words
@@ -117,7 +118,7 @@ struct IfaceDF {
   __device__ float2* piL() const { return reinterpret_cast<float2*>(base + O.piL); }
   __device__ float2* wR() const { return reinterpret_cast<float2*>(base + O.wR); }
   __device__ float2* wL() const { return reinterpret_cast<float2*>(base + O.wL); }
-  __device__ float2* xch() const { return reinterpret_cast<float2*>(base + O.xch); }
+  __device__ float2* xch() const { return xg ? xg : reinterpret_cast<float2*>(base + O.xch); }
   __device__ float* xin() const { return reinterpret_cast<float*>(base + O.xin); }
   __device__ uint64_t* xbar() const { return reinterpret_cast<uint64_t*>(base + O.xbar); }
   __device__ float2* in() const { return reinterpret_cast<float2*>(base + O.in); }
@@ -378,20 +379,27 @@ __device__ __forceinline__ void iface_push_fold(const IfaceDF<R, MM, false>& f, 
   }
 }
 
-// in_R, in_L of every column from the other CTAs' totals (after a cluster
-// barrier): one warp per column, lanes 0-15 for the CTAs to the left, 16-31
-// for those to the right.  The C CTAs that share the tile are cluster ranks
-// base .. base + C - 1; c is this CTA's place among them.
-template <int R, int MM, bool PAIR = true, bool AP = PAIR>
+// The cluster's CTAs as the peers of a tile: loads from the same
+// shared-memory offset in another CTA.
+struct ClusterPeers {
+  __device__ float2 ld2(const float2* mine, unsigned rank) const { return ld_cluster_f32x2(mine, rank); }
+};
+
+// in_R, in_L of every column from the other CTAs' totals (after the barrier
+// that published them): one warp per column, lanes 0-15 for the CTAs to the
+// left, 16-31 for those to the right.  The C CTAs that share the tile are
+// ranks base .. base + C - 1 of the peers `pe` (a cluster, or a group of a
+// cooperative launch); c is this CTA's place among them.
+template <int R, int MM, bool PAIR = true, bool AP = PAIR, class P = ClusterPeers>
 __device__ __forceinline__ void iface_df_fold(const IfaceDF<R, MM, PAIR>& f, int C, unsigned c, int parity,
-                                              unsigned base = 0) {
+                                              unsigned base = 0, const P& pe = P{}) {
   const int lane = threadIdx.x & 31, cc = lane & 15;
   const bool left = lane < 16;
   const bool valid = left ? (cc < (int)c) : (cc > (int)c && cc < C);
   for (int r = threadIdx.x >> 5; r < R; r += blockDim.x >> 5) {
     f2pair v{0.f, 0.f};
     if (valid) {
-      const float2 x = ld_cluster_f32x2(f.xch() + (parity * 2 + (left ? 0 : 1)) * R + r, base + (unsigned)cc);
+      const float2 x = pe.ld2(f.xch() + (parity * 2 + (left ? 0 : 1)) * R + r, base + (unsigned)cc);
       v = mfma<AP>(mld<AP>(left ? &f.wR()[cc] : &f.wL()[cc]), fp(x), f2pair{0.f, 0.f});
     }
 #pragma unroll

@@ -65,6 +65,11 @@ struct tdm_plan_s {
   double* piv = nullptr;      // [4n] forward and backward pivots of A (double-double)
   unsigned long long* stat = nullptr;  // [8] device status / reductions
   int* dev_err = nullptr;     // [1] device error word of solves
+  // cooperative refined launches (tdm_refine.cu): CTAs of the grid, their
+  // scratch blocks and the groups' barrier counters
+  int coop_grid = 0;
+  float* coop_scr = nullptr;
+  unsigned* coop_ctr = nullptr;
   cudaEvent_t last = nullptr; // recorded after each solve
   void* host_stage = nullptr; // staging buffers and streams of tdm_solve_host (created on first use)
   // two levels (n beyond one cluster, tdm_large.cu): segments, their plans, responses, reduced plan

@@ -423,7 +423,7 @@ static void tdm_free_plan(tdm_plan_s* p) {
   if (!p) return;
   cudaFree(p->coef64); cudaFree(p->coef32); cudaFree(p->res32); cudaFree(p->rtab);
   cudaFree(p->rR); cudaFree(p->rL); cudaFree(p->a64); cudaFree(p->b64); cudaFree(p->tr);
-  cudaFree(p->piv); cudaFree(p->stat); cudaFree(p->dev_err);
+  cudaFree(p->piv); cudaFree(p->stat); cudaFree(p->dev_err); cudaFree(p->coop_scr); cudaFree(p->coop_ctr);
   if (p->last) cudaEventDestroy(p->last);
   tdm_host_stage_free(p->host_stage);
   if (p->nseg > 0) tdm_free_large(p);
@@ -562,6 +562,17 @@ static tdm_status prepare_plan(const double* a, const double* b, const double* s
             cudaMalloc(&p->stat, sizeof(unsigned long long) * 8) == cudaSuccess &&
             cudaMalloc(&p->dev_err, sizeof(int)) == cudaSuccess &&
             cudaEventCreateWithFlags(&p->last, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && !general) {   // a cooperative launch's scratch, where the rule prefers it to clusters
+    RefShape sh;
+    if (tdm_refined_shape(p->M, t, tile, sh) && sh.C > 1) {
+      const int grid = tdm_refined_coop_choice(sh, t);
+      if (grid > 0) {
+        ok = cudaMalloc(&p->coop_scr, tdm_refined_coop_scratch(sh, grid)) == cudaSuccess &&
+             cudaMalloc(&p->coop_ctr, sizeof(unsigned) * 32 * (grid / sh.C)) == cudaSuccess;
+        p->coop_grid = grid;
+      }
+    }
+  }
   if (!ok) {
     (void)cudaGetLastError();
     tdm_free_plan(p);

@@ -46,6 +46,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -76,10 +77,107 @@ constexpr float kRefineTol = 1e-12f;
 constexpr float kRefineTol1 = 4e-12f;
 constexpr int kRefineCap = 4;
 
+// The peers of a tile and their barrier.
+//  * Cluster (COOP false): the CTAs of the thread-block cluster.  Barriers are
+//    the hardware cluster barrier; what the peers read sits in shared memory
+//    and is read through the cluster's shared-memory window.
+//  * Group (COOP true): g consecutive CTAs of a cooperative launch (every CTA
+//    of the grid resident at once).  A barrier is a counter in global memory:
+//    each CTA, after its writes, adds 1 with release semantics, and waits
+//    until the count reaches its own arrivals times g (a bounded spin by one
+//    thread; on time-out it records kDevErrGroupTimeout and stops waiting).
+//    What the peers read sits in a scratch block of kScr floats per CTA in
+//    global memory, read with gpu-scope loads (not through L1) after the
+//    barrier.  Ranks are group-relative: rank k is the CTA first + k.
+constexpr int kGroupSpinLimit = 1 << 21;
+template <bool COOP>
+struct Link {
+  unsigned me = 0;         // this CTA's index in the grid (COOP)
+  unsigned first = 0;      // the grid index of the group's rank 0 (COOP)
+  int stride = 0;          // floats between consecutive CTAs' scratch blocks (COOP)
+  unsigned g = 0;          // CTAs of the group (COOP)
+  unsigned* ctr = nullptr; // the group's counter (COOP)
+  int* err = nullptr;
+  unsigned narr = 0;       // this CTA's arrivals so far
+  bool broken = false;     // a wait timed out (thread 0)
+  __device__ const float* at(const float* mine, unsigned rank) const {
+    return mine + ((int)(first + rank) - (int)me) * stride;
+  }
+  __device__ float ld(const float* mine, unsigned rank) const {
+    if constexpr (COOP) {
+      float v;
+      asm volatile("ld.relaxed.gpu.f32 %0, [%1];" : "=f"(v) : "l"(at(mine, rank)) : "memory");
+      return v;
+    } else {
+      return ld_cluster_f32(mine, rank);
+    }
+  }
+  __device__ float2 ld2(const float2* mine, unsigned rank) const {
+    if constexpr (COOP) {
+      const float* p = at(reinterpret_cast<const float*>(mine), rank);
+      float2 v;
+      asm volatile("ld.relaxed.gpu.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
+      return v;
+    } else {
+      return ld_cluster_f32x2(mine, rank);
+    }
+  }
+  __device__ void arrive() {
+    if constexpr (COOP) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+      }
+      narr++;
+    } else {
+      cluster_arrive();
+    }
+  }
+  __device__ void wait() {
+    if constexpr (COOP) {
+      if (threadIdx.x == 0 && !broken) {
+        const unsigned target = narr * g;
+        for (int it = 0;; it++) {
+          unsigned v;
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+          if (v >= target) break;
+          if (it >= kGroupSpinLimit) {
+            broken = true;
+            atomicExch(err, kDevErrGroupTimeout);
+            break;
+          }
+          if (it >= 32) __nanosleep(64);
+        }
+      }
+      __syncthreads();
+    } else {
+      cluster_wait();
+    }
+  }
+  __device__ void barrier() {
+    if constexpr (COOP) {
+      arrive();
+      wait();
+    } else {
+      cluster_barrier();
+    }
+  }
+};
+
+// Scratch block of a CTA of a cooperative launch (floats): the A4 totals
+// [2 parity][2 dir][R] pairs, the edge rows of x (first block: high, low;
+// last block: high, low) [4][R], the correction maxima [4][kSlot], the
+// speculative maxima [kVerSlots][kSlot].
 // Slots of per-CTA maxima that the other CTAs of the cluster read: [2][R]
 // (max|d| and max|x| of every column), then the size of the CTA's group and
 // its item's contraction.
 __host__ __device__ constexpr int kSlot(int R) { return 2 * R + 2; }
+constexpr int kVerSlots = 4;   // rotating slots of speculative units' maxima
+__host__ __device__ constexpr int kScrEdge(int R) { return 8 * R; }
+__host__ __device__ constexpr int kScrCvg(int R) { return 12 * R; }
+__host__ __device__ constexpr int kScrVer(int R) { return 12 * R + 4 * kSlot(R); }
+__host__ __device__ constexpr int kScr(int R) { return (12 * R + (4 + kVerSlots) * kSlot(R) + 31) / 32 * 32; }
 
 // Relative size max|d| / max|x| of every column for each group of CTAs (the
 // maxima taken over the group's CTAs), times the group's contraction when
@@ -92,20 +190,20 @@ __host__ __device__ constexpr int kSlot(int R) { return 2 * R + 2; }
 // must have been published by a cluster barrier.
 // Without groups (GROUPED false) every CTA belongs to the one group of all CL
 // CTAs and shares the contraction kc0: nothing but the maxima is read.
-template <int R, bool GROUPED>
+template <int R, bool GROUPED, class LK>
 __device__ __forceinline__ void group_ratios(const float* slot, int CL, unsigned cphys, bool scale, float kc0,
-                                             float* out, float* own) {
+                                             float* out, float* own, const LK& lk) {
   const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const unsigned cc = lane & 15;
   const bool have = (int)cc < CL;
   int gs = CL;
   float kc = scale ? kc0 : 1.f;
   if constexpr (GROUPED) {
-    gs = have ? (int)ld_cluster_f32(slot + 2 * R, cc) : 1;
-    kc = have && scale ? ld_cluster_f32(slot + 2 * R + 1, cc) : 1.f;
+    gs = have ? (int)lk.ld(slot + 2 * R, cc) : 1;
+    kc = have && scale ? lk.ld(slot + 2 * R + 1, cc) : 1.f;
   }
   for (int col = threadIdx.x >> 5; col < R; col += nwarps) {
-    float v = have ? ld_cluster_f32(slot + (lane >> 4) * R + col, cc) : 0.f;
+    float v = have ? lk.ld(slot + (lane >> 4) * R + col, cc) : 0.f;
 #pragma unroll
     for (int o = 8; o >= 1; o >>= 1) {
       const float w = __shfl_xor_sync(0xffffffffu, v, o);
@@ -443,7 +541,6 @@ __device__ __forceinline__ void output(float2 (&g)[TT / 2], const float2 (&xh)[T
 struct RefOffsets {
   size_t tab, xl, edge, red, cvg, ver, iface, bytes;
 };
-constexpr int kVerSlots = 4;   // rotating slots of speculative tiles' maxima
 __host__ __device__ constexpr RefOffsets refine_offsets(int R, int TT, int NT, bool sm_coef) {
   const size_t MM = (size_t)(NT / R);
   RefOffsets o{};
@@ -479,8 +576,10 @@ enum { kFixed = 0, kSpec = 1, kTested = 2, kRetry = 3, kCalib = 4, kRetryFixed =
 
 // Launch modes: one series (its tile i is unit i); a list of items, one per
 // unit, every CTA of the cluster on it (items of one cluster width, each with
-// its own blocks per CTA); grouped units (an item per CTA).
-enum { kLaunchSingle = 0, kLaunchList = 1, kLaunchGrouped = 2 };
+// its own blocks per CTA); grouped units (an item per CTA); one series in a
+// cooperative launch without clusters (groups of C consecutive CTAs take the
+// place of clusters, see Link).
+enum { kLaunchSingle = 0, kLaunchList = 1, kLaunchGrouped = 2, kLaunchCoop = 3 };
 
 template <int R, int TT, int NT, int MINB, bool SM, int LM>
 __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
@@ -499,32 +598,46 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   float* const eLh = eFl + MM * R;
   float* const eLl = eLh + MM * R;
   float* const red = reinterpret_cast<float*>(smem_raw + O.red);     // [2][warps][R] per-warp maxima
-  float* const cvg = reinterpret_cast<float*>(smem_raw + O.cvg);     // [4][SL] maxima of corrections, read remotely
-  float* const cvg_all = cvg + 4 * SL;                               // [R] largest ratio over the groups
-  float* const cvg_own = cvg_all + R;                                // [R] ratio of this CTA's group
-  float* const ver = reinterpret_cast<float*>(smem_raw + O.ver);     // [kVerSlots][SL] speculative units' maxima
-  float* const ver_all = ver + kVerSlots * SL;                       // [R]
-  const IfaceDF<R, MM, true> f{smem_raw + O.iface};
-  const unsigned cphys = cluster_rank();
+  constexpr bool coop = LM == kLaunchCoop;
+  constexpr bool one_series = LM == kLaunchSingle || LM == kLaunchCoop;
+  constexpr bool grouped = LM == kLaunchGrouped;
+  // what the peers read: shared memory, or this CTA's scratch block (coop)
+  float* const scr = coop ? L.scr + (size_t)blockIdx.x * kScr(R) : nullptr;
+  float* const cvg = coop ? scr + kScrCvg(R) : reinterpret_cast<float*>(smem_raw + O.cvg);   // [4][SL] maxima of corrections
+  float* const cvg_all = reinterpret_cast<float*>(smem_raw + O.cvg) + 4 * SL;               // [R] largest ratio over the groups
+  float* const cvg_own = cvg_all + R;                                                        // [R] ratio of this CTA's group
+  float* const ver = coop ? scr + kScrVer(R) : reinterpret_cast<float*>(smem_raw + O.ver);   // [kVerSlots][SL] speculative maxima
+  float* const ver_all = reinterpret_cast<float*>(smem_raw + O.ver) + kVerSlots * SL;        // [R]
+  float* const scr_e = coop ? scr + kScrEdge(R) : nullptr;                                   // [4][R] edge rows of x
+  const IfaceDF<R, MM, true> f{smem_raw + O.iface, coop ? reinterpret_cast<float2*>(scr) : nullptr};
   const int tid = threadIdx.x;
   const int r = tid % R;
   const int bl = tid / R;
-  const int CL = L.C;
+  const int CL = L.C;                          // CTAs per cluster, or per group (coop)
+  const unsigned cphys = coop ? blockIdx.x % CL : cluster_rank();
   const int cluster_id = blockIdx.x / CL;
   const int nclusters = gridDim.x / CL;
-  constexpr bool grouped = LM == kLaunchGrouped;
+  Link<coop> lk;
+  if constexpr (coop) {
+    lk.me = blockIdx.x;
+    lk.first = (unsigned)(cluster_id * CL);
+    lk.stride = kScr(R);
+    lk.g = (unsigned)CL;
+    lk.ctr = L.ctr + 32 * cluster_id;
+    lk.err = L.err;
+  }
   float* const xlp = sxl + tid * XLS;
   // Threads past the CTA's blocks (bl >= m) only round the CTA up to whole
   // warps; they run the same code on zero coefficients and zero data.
   for (int k = tid; k < kVerSlots * SL; k += blockDim.x) ver[k] = 0.f;   // published by the first cluster barrier
 
-#define ITEMX(i, fld) (LM == kLaunchSingle ? L.one.fld : L.items[i].fld)
+#define ITEMX(i, fld) (one_series ? L.one.fld : L.items[i].fld)
   // the item this CTA works on in unit u, and the first rank of its group
   auto item_of = [&](int u) -> int { return grouped ? L.units[u * kUnitW + cphys] : u; };
   auto group_base = [&](int gs) -> unsigned { return grouped ? (cphys & ~(unsigned)(gs - 1)) : 0u; };
   // largest ratio over the groups (every CTA the same) and this CTA's group's
   auto ratios = [&](const float* slot, float& own) -> float {
-    group_ratios<R, grouped>(slot, CL, cphys, false, 1.f, cvg_all, cvg_own);
+    group_ratios<R, grouped>(slot, CL, cphys, false, 1.f, cvg_all, cvg_own, lk);
     __syncthreads();
     float q = 0.f, o = 0.f;
     for (int k = 0; k < R; k++) {
@@ -537,7 +650,7 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   };
   // verdict on the last speculative unit (slot published by a cluster barrier)
   auto verified = [&](int vs, float kc0) -> bool {
-    group_ratios<R, grouped>(ver + vs * SL, CL, cphys, true, kc0, ver_all, nullptr);
+    group_ratios<R, grouped>(ver + vs * SL, CL, cphys, true, kc0, ver_all, nullptr, lk);
     __syncthreads();
     float q = 0.f;
     for (int k = 0; k < R; k++) q = fmaxf(q, ver_all[k]);
@@ -566,7 +679,7 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       u = u_next;
       u_next += u_step;
     } else if (unverified >= 0) {   // the last speculative unit: check it now
-      cluster_barrier();
+      lk.barrier();
       if (!verified(vslot, ITEMX(item_of(unverified), contraction))) pending = unverified;
       unverified = -1;
       __syncthreads();
@@ -578,21 +691,21 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
     // of a single-series launch, else a copy in shared memory (cheap to read
     // again after every barrier instead of held in registers through the tile)
     const int it = item_of(u);
-    if constexpr (LM != kLaunchSingle) {
+    if constexpr (!one_series) {
       __syncthreads();   // every read of the previous item's copy is done
       if (tid < (int)(sizeof(RefItem) / 4))
         reinterpret_cast<int*>(&s_item)[tid] = __ldg(reinterpret_cast<const int*>(L.items + it) + tid);
       __syncthreads();
     }
-#define ITEM(fld) (LM == kLaunchSingle ? L.one.fld : s_item.fld)
+#define ITEM(fld) (one_series ? L.one.fld : s_item.fld)
     // pointers and strides read again at every use (from the copy), so that no
     // address is held in registers through the tile
-#define ITEMV(fld) (LM == kLaunchSingle ? L.one.fld : *(volatile decltype(s_item.fld)*)&s_item.fld)
+#define ITEMV(fld) (one_series ? L.one.fld : *(volatile decltype(s_item.fld)*)&s_item.fld)
     const int gs = grouped ? ITEM(g) : CL;   // CTAs of the group
-    const int m = LM == kLaunchSingle ? L.m : ITEM(m);   // blocks per CTA
+    const int m = one_series ? L.m : ITEM(m);   // blocks per CTA
     const unsigned base = group_base(gs);    // the group's first rank
     const unsigned c = cphys - base;         // rank in the group
-    const int tile = LM == kLaunchSingle ? u : ITEM(tile);
+    const int tile = one_series ? u : ITEM(tile);
     const int M = ITEM(M);
     // new series or new place in the group: ratios, products, coefficient
     // rows (a null item, M = 0, needs none: its threads have no rows)
@@ -654,10 +767,10 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       f.beL()[bl * f.kRP + r] = bL;
       __syncthreads();
       iface_df_scan<R, MM, true, true>(f, m, parity);
-      cluster_arrive();   // the back substitution overlaps the exchange of the CTA totals
+      lk.arrive();   // the back substitution overlaps the exchange of the CTA totals
       backward_y<TT, SM>(g, cb);
-      cluster_wait();
-      iface_df_fold<R, MM, true, true>(f, gs, c, parity, base);
+      lk.wait();
+      iface_df_fold<R, MM, true, true>(f, gs, c, parity, base, lk);
       // the exchange also published the last speculative unit's maxima; every
       // CTA reaches the same verdict from the same maxima
       if (unverified >= 0) {
@@ -684,9 +797,9 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       Rows<const float> fn{ITEMV(F), 0, 0};
       if (nu >= 0) {
         const int itn = item_of(nu);
-        const int gn = grouped ? ITEMX(itn, g) : CL, mn = LM == kLaunchSingle ? L.m : ITEMX(itn, m);
+        const int gn = grouped ? ITEMX(itn, g) : CL, mn = one_series ? L.m : ITEMX(itn, m);
         const int bn = (int)(cphys - group_base(gn)) * mn + bl;
-        const int tile_n = LM == kLaunchSingle ? nu : L.items[itn].tile;
+        const int tile_n = one_series ? nu : L.items[itn].tile;
         const int64_t col_n = (int64_t)tile_n * R + r;
         const int64_t row0_n = (int64_t)bn * TT;
         const int n_n = ITEMX(itn, n);
@@ -708,12 +821,22 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       eFl[bl * R + r] = ldxl(xlp, 0).x;
       eLh[bl * R + r] = xh[H - 1].y;
       eLl[bl * R + r] = ldxl(xlp, H - 1).y;
+      if constexpr (coop) {   // the rows the neighbouring CTAs read
+        if (bl == 0) {
+          scr_e[r] = xh[0].x;
+          scr_e[R + r] = ldxl(xlp, 0).x;
+        }
+        if (bl == m - 1) {
+          scr_e[2 * R + r] = xh[H - 1].y;
+          scr_e[3 * R + r] = ldxl(xlp, H - 1).y;
+        }
+      }
       // Tests read every CTA's maxima of the last correction: a full cluster
       // barrier, which also publishes the edge values.  Otherwise the interior
       // of the residual overlaps the edge-value barrier.
       const bool test = intest && done >= (mode == kRetry ? 2 : 1);
       if (test) {
-        cluster_barrier();
+        lk.barrier();
         float own;
         const float ratio = ratios(cvg + (done & 1) * SL, own);
         if (mode == kCalib && tid == 0 && c == 0) atomicMax(&g_tdm_calib[done - 1], __float_as_uint(ratio));
@@ -725,11 +848,11 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       } else {
         if (mode == kRetry && done == 1)   // the ratio test of correction 2 needs ratio_1
           ratio_prev = 0.f;
-        cluster_arrive();
+        lk.arrive();
       }
       df2 E0, Elast;
       residual_interior<TT, SM>(g, xh, xlp, cb, E0, Elast);
-      if (!test) cluster_wait();
+      if (!test) lk.wait();
       if (mode == kRetry && done == 1) {
         float own;
         ratio_prev = ratios(cvg + (done & 1) * SL, own);
@@ -738,13 +861,19 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       if (bl > 0) {
         xm = f2pair{eLh[(bl - 1) * R + r], eLl[(bl - 1) * R + r]};
       } else if (c > 0) {
-        xm = f2pair{ld_cluster_f32(eLh + (m - 1) * R + r, base + c - 1),
-                    ld_cluster_f32(eLl + (m - 1) * R + r, base + c - 1)};
+        if constexpr (coop)
+          xm = f2pair{lk.ld(scr_e + 2 * R + r, c - 1), lk.ld(scr_e + 3 * R + r, c - 1)};
+        else
+          xm = f2pair{ld_cluster_f32(eLh + (m - 1) * R + r, base + c - 1),
+                      ld_cluster_f32(eLl + (m - 1) * R + r, base + c - 1)};
       }
       if (bl < m - 1) {
         xp = f2pair{eFh[(bl + 1) * R + r], eFl[(bl + 1) * R + r]};
       } else if ((int)c < gs - 1) {
-        xp = f2pair{ld_cluster_f32(eFh + r, base + c + 1), ld_cluster_f32(eFl + r, base + c + 1)};
+        if constexpr (coop)
+          xp = f2pair{lk.ld(scr_e + r, c + 1), lk.ld(scr_e + R + r, c + 1)};
+        else
+          xp = f2pair{ld_cluster_f32(eFh + r, base + c + 1), ld_cluster_f32(eFl + r, base + c + 1)};
       }
       residual_edges<TT, SM>(g, xh, xlp, cb, xm, xp, E0, Elast);
 
@@ -755,10 +884,10 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
       f.beL()[bl * f.kRP + r] = bL;
       __syncthreads();
       iface_df_scan<R, MM, true, false>(f, m, parity);
-      cluster_arrive();
+      lk.arrive();
       backward_y<TT, SM>(g, cb);
-      cluster_wait();
-      iface_df_fold<R, MM, true, false>(f, gs, c, parity, base);
+      lk.wait();
+      iface_df_fold<R, MM, true, false>(f, gs, c, parity, base, lk);
       __syncthreads();
       parity ^= 1;
       float xL = 0.f, xR = 0.f;
@@ -806,7 +935,7 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
     }
     if (!fused_out) {
       if (track && done == cap) {   // cap reached: record the last correction
-        cluster_barrier();
+        lk.barrier();
         if (mode == kRetryFixed) {   // per group: would the tested criterion have stopped by now?
           float prev, cur;
           ratios(cvg, prev);
@@ -836,8 +965,9 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
 #undef ITEM
   }
 #undef ITEMX
-  // no CTA may leave while a peer can still read its shared memory
-  cluster_barrier();
+  // no CTA may leave while a peer can still read its shared memory (the
+  // scratch blocks of a cooperative launch stay readable)
+  if constexpr (!coop) cluster_barrier();
 }
 
 template <int R_, int TT_, int NT_, int MINB_, bool SM_>
@@ -925,6 +1055,12 @@ struct RefCand {
   int R, NT;
   bool sm;
 };
+// A single-series solve runs as a cooperative launch when that holds at least
+// kCoopGain times the CTAs that clusters of its width can (clusters of 16 CTAs
+// leave a quarter of the GPU's CTA slots idle on GB300, clusters of up to 8
+// almost none, and a group barrier in global memory costs more than the
+// hardware cluster barrier).
+constexpr double kCoopGain = 1.2;
 // the shapes of each block size, in the rule's order
 constexpr RefCand kCand32[] = {{8, 256, true}, {8, 512, true}, {4, 512, false}, {16, 512, true}};
 constexpr RefCand kCand16[] = {{8, 256, true}, {8, 512, true}, {4, 1024, false}};
@@ -1011,6 +1147,76 @@ tdm_status tdm_refined_launch_grouped(const RefShape& sh, int t, const RefItem* 
   return st;
 }
 
+int tdm_refined_coop_grid(const RefShape& sh, int t) {
+  int grid = 0;
+  with_shape(sh, t, [&](auto tag) {
+    using S = decltype(tag);
+    auto kern = refined_kernel<S, kLaunchCoop>();
+    int dev = 0, sms = 0, nb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, sh.threads, sh.smem) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return;
+    }
+    grid = (nb * sms / sh.C) * sh.C;
+  });
+  return grid;
+}
+
+size_t tdm_refined_coop_scratch(const RefShape& sh, int grid) { return sizeof(float) * (size_t)grid * kScr(sh.R); }
+
+int tdm_refined_coop_choice(const RefShape& sh, int t) {
+  if (sh.C < 2) return 0;
+  int slots = 0;
+  if (!with_shape(sh, t, [&](auto tag) { slots = shape_max_clusters<decltype(tag), kLaunchSingle>(sh) * sh.C; }))
+    return 0;
+  const int grid = tdm_refined_coop_grid(sh, t);
+  return (double)grid >= kCoopGain * (double)slots ? grid : 0;
+}
+
+tdm_status tdm_refined_launch_coop(const RefShape& sh, int t, const RefItem& one, int ntiles, int* err, float* scr,
+                                   unsigned* ctr, int grid, cudaStream_t s) {
+  if (ntiles <= 0) return TDM_OK;
+  RefLaunch L;
+  memset(&L, 0, sizeof(L));
+  L.one = one;
+  L.one.m = sh.m;
+  L.one.g = sh.C;
+  L.nitems = ntiles;
+  L.single = 1;
+  L.m = sh.m;
+  L.C = sh.C;
+  L.err = err;
+  L.scr = scr;
+  L.ctr = ctr;
+  // no more groups than tiles
+  const int groups = std::min(grid / sh.C, ntiles);
+  TDM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned) * 32 * groups, s));
+  tdm_status st = TDM_OK;
+  if (!with_shape(sh, t, [&](auto tag) {
+        using S = decltype(tag);
+        auto kern = refined_kernel<S, kLaunchCoop>();
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
+          st = TDM_ERR_CUDA;
+          return;
+        }
+        cudaLaunchConfig_t lc = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        lc.gridDim = dim3(groups * sh.C);
+        lc.blockDim = dim3(sh.threads);
+        lc.dynamicSmemBytes = sh.smem;
+        lc.stream = s;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        if (cudaLaunchKernelEx(&lc, kern, L) != cudaSuccess) st = TDM_ERR_CUDA;
+      }))
+    return TDM_ERR_NOT_IMPLEMENTED;
+  return st;
+}
+
 int tdm_refined_max_clusters(const RefShape& sh, int t) {
   int maxc = 0;
   if (!with_shape(sh, t, [&](auto tag) { maxc = shape_max_clusters<decltype(tag), kLaunchGrouped>(sh); })) return 0;
@@ -1033,12 +1239,14 @@ RefItem tdm_refined_item(const tdm_plan_s* p, const float* F, int64_t ldF, doubl
 }
 
 tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX, int64_t N,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool allow_coop) {
   if (ldF > kRefMaxLd || ldX > kRefMaxLd) return TDM_ERR_NOT_IMPLEMENTED;
   RefShape sh;
   if (!tdm_refined_shape(p->M, p->t, p->tile_rhs, sh)) return TDM_ERR_NOT_IMPLEMENTED;
   const RefItem one = tdm_refined_item(p, F, ldF, X, ldX, N, 0, sh);
   const int ntiles = (int)((N + sh.R - 1) / sh.R);
+  if (allow_coop && p->coop_grid > 0)
+    return tdm_refined_launch_coop(sh, p->t, one, ntiles, p->dev_err, p->coop_scr, p->coop_ctr, p->coop_grid, s);
   return tdm_refined_launch(sh, p->t, nullptr, &one, ntiles, p->dev_err, s);
 }
 

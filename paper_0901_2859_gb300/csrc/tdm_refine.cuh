@@ -64,8 +64,10 @@ struct RefLaunch {
   RefItem one;            // the series of a single-series launch (item i = its tile i)
   int nitems;             // single: tiles; list: items (cluster k takes k, k + clusters, ...)
   int single;
-  int m, C;               // single: blocks per CTA; CTAs per cluster
+  int m, C;               // single: blocks per CTA; CTAs per cluster (per group: cooperative)
   int* err;
+  float* scr;             // cooperative: scratch blocks of the CTAs
+  unsigned* ctr;          // cooperative: barrier counters of the groups (zero at launch)
 };
 
 // tile shape of the refined kernel for a series of M blocks of t rows
@@ -96,9 +98,21 @@ tdm_status tdm_refined_launch_grouped(const RefShape& sh, int t, const RefItem* 
                                       const int* ustart, int nclusters, int* err, cudaStream_t s);
 // clusters of sh.C CTAs of the shape's kernel that the device holds at once
 int tdm_refined_max_clusters(const RefShape& sh, int t);
-// the refined solve of one series (one single-series launch)
+// Cooperative launches of one series (groups of sh.C consecutive CTAs in
+// place of clusters): the largest grid of whole groups the device holds at
+// once (0 if none), the bytes of scratch that grid needs, and the launch (its
+// counters are zeroed on the stream first).
+int tdm_refined_coop_grid(const RefShape& sh, int t);
+// the cooperative grid when the rule prefers it to clusters for this shape, else 0
+int tdm_refined_coop_choice(const RefShape& sh, int t);
+size_t tdm_refined_coop_scratch(const RefShape& sh, int grid);
+tdm_status tdm_refined_launch_coop(const RefShape& sh, int t, const RefItem& one, int ntiles, int* err, float* scr,
+                                   unsigned* ctr, int grid, cudaStream_t s);
+// the refined solve of one series (one single-series launch; cooperative when
+// the plan chose it at prepare and allow_coop is set -- not for launches that
+// run side by side with others, which a cooperative grid cannot share the GPU with)
 tdm_status tdm_launch_refined(tdm_plan_s* p, const float* F, int64_t ldF, double* X, int64_t ldX, int64_t N,
-                              cudaStream_t s);
+                              cudaStream_t s, bool allow_coop = true);
 // the calibration record: max over tiles of max|d_k| / max|x| for corrections
 // k = 1 .. kRefineCalibSteps of calibration solves (cleared, or read into ratios)
 tdm_status tdm_calibration_record(bool clear, float* ratios, cudaStream_t s);

@@ -8,7 +8,7 @@
 #include <stdint.h>
 
 // device error codes written to the plan's error word
-enum { kDevErrTmaTimeout = 1, kDevErrNotConverged = 2 };
+enum { kDevErrTmaTimeout = 1, kDevErrNotConverged = 2, kDevErrGroupTimeout = 3 };
 
 // Encode a row-major [rows][cols] tensor with row pitch `ld_bytes` and a box
 // of [box_rows][box_cols].  Returns false when the layout cannot be described

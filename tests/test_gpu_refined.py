@@ -178,3 +178,41 @@ def test_largest_refined_size_and_the_next(tdm, dev, oracle):
     F2 = s2.F.astype(np.float32)
     ref2 = oracle.solve_hi(s2.a, s2.b, F2.astype(np.float64))
     assert relerr(_refined(tdm, dev, s2.a, s2.b, F2), ref2) <= TOL
+
+
+@pytest.mark.parametrize("n,N", [(12289, 37), (16384, 300)])
+def test_cooperative_launch_matches_clusters(tdm, dev, oracle, n, N):
+    """Plans that need clusters of 13 to 16 CTAs solve in a cooperative launch
+    (CTA groups exchanging through global memory).  The same plan solved with
+    clusters -- the per-series batched layout never uses the cooperative
+    launch -- gives the same result bit for bit, and it meets the gate; a CUDA
+    graph that captured the cooperative solve replays it exactly."""
+    from paper_0901_2859_gb300 import workloads
+    s = workloads.precision(seed=5, n=n, N=N, s=1e-6)
+    plan = tdm.prepare(s.a, s.b, device=dev)
+    F = torch.from_numpy(s.F).to(dev)
+    Xc = plan.solve(F, "fp32_refined")
+    tdm.set_batched_strategy("per_series")
+    try:
+        Xk = tdm.solve_batched([plan], [F], "fp32_refined")[0]
+    finally:
+        tdm.set_batched_strategy("auto")
+    torch.cuda.synchronize()
+    assert torch.equal(Xc, Xk)
+    cols = np.r_[0:4, N - 4:N]
+    ref = oracle.solve_hi(s.a, s.b, np.ascontiguousarray(s.F[:, cols], dtype=np.float64))
+    assert relerr(Xc[:, cols].cpu().numpy(), ref) <= TOL
+    out = torch.empty_like(Xc)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        plan.solve(F, "fp32_refined", out=out)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        plan.solve(F, "fp32_refined", out=out)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, Xc)
+    assert plan.info()["device_error"] == 0
+    plan.close()
