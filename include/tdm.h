@@ -227,8 +227,13 @@ tdm_status tdm_solve_batched(const tdm_handle* hs, int count,
  *      clusters are as wide as the widest series needs, and each walks a list
  *      of units in which tiles of several series run side by side, each on an
  *      aligned power-of-two group of CTAs.
+ *   4  one cooperative persistent launch per kernel shape over every CTA the
+ *      GPU holds at once, without clusters: each series keeps its own
+ *      partition (g CTAs), its tiles are cut into runs placed on windows of g
+ *      consecutive CTAs, and each run's CTAs exchange values through global
+ *      memory and a barrier counter of the run.
  * Under each, a series with a fixed or calibrated refinement gets the result
- * of its own tdm_solve, bit for bit; under 1, a plan with the uncalibrated
+ * of its own tdm_solve, bit for bit (under 4 any series does); under 1, a plan with the uncalibrated
  * per-tile test (refine_steps = -1 requested), and a unit whose speculative
  * check fails, run four corrections and a convergence check.
  * Errors: TDM_ERR_INVALID_ARG for any other value. */

@@ -187,7 +187,7 @@ def prepare(a, b, block_rows: int = 0, refine_steps: int = 0, device=None, tile_
     return Plan(a, b, block_rows=block_rows, refine_steps=refine_steps, tile_rhs=tile_rhs)
 
 
-BATCHED_STRATEGIES = {"by_width": 0, "grouped": 1, "per_series": 2, "auto": 3}
+BATCHED_STRATEGIES = {"by_width": 0, "grouped": 1, "per_series": 2, "auto": 3, "cooperative": 4}
 
 
 def set_batched_strategy(strategy: str) -> None:

@@ -2,7 +2,7 @@
 // right-hand sides (the per-mode series of the Fourier method, Section 4,
 // eqs. series_fft, poisson_end), solved by the refined persistent kernel.
 //
-// Three ways to lay the work out (tdm_set_batched_strategy; by default a rule
+// Four ways to lay the work out (tdm_set_batched_strategy; by default a rule
 // picks the first for batches that need many launch classes, the second for
 // those that need few, such as the equal-size modes of one Poisson problem):
 //
@@ -31,7 +31,11 @@
 //    corrections: series with different schedules (fixed counts, the
 //    speculative test) go to different launches.
 //
-// All three give every series the result of its own tdm_solve, bit for bit
+//  * cooperative runs: one cooperative launch per kernel shape over every CTA
+//    the GPU holds, with groups of consecutive CTAs in place of clusters
+//    (see build_coop), so that no CTA slot is lost to cluster placement.
+//
+// All of them give every series the result of its own tdm_solve, bit for bit
 // (the grouped units differ only where a tile is solved again, see
 // tdm_set_batched_strategy).  Work lists are built on the host on first use of
 // an argument set and kept until one of their plans is destroyed, so repeated
@@ -57,12 +61,16 @@ namespace {
 struct GroupedLaunch {
   RefShape sh;        // the kernel's shape; C = CTAs per cluster
   int t = 0;
-  int nclusters = 0;  // grouped: clusters; list: items
+  int nclusters = 0;  // grouped: clusters; list: items; cooperative: CTAs
   bool grouped = false;
+  bool coop = false;  // a cooperative launch over runs
+  int nruns = 0;
   size_t items_off = 0, units_off = 0, ustart_off = 0;   // byte offsets into the work list buffer
+  size_t runs_off = 0, scr_off = 0, ctr_off = 0;         // cooperative: runs, scratch, counters
 };
 
-std::atomic<int> g_strategy{3};   // 0: by cluster width, 1: grouped units, 2: one launch per series, 3: by rule
+// 0: by cluster width, 1: grouped units, 2: one launch per series, 3: by rule, 4: cooperative runs
+std::atomic<int> g_strategy{3};
 
 struct WorkList {
   std::vector<uint64_t> key;
@@ -336,10 +344,145 @@ Helpers* helpers_of(int dev) {
   return &x;
 }
 
+// Cooperative runs: one launch per kernel shape over all CTAs the device
+// holds.  Every series keeps its single-series partition (g = its CTAs per
+// cluster, m its blocks per CTA) and is cut into runs of consecutive tiles;
+// a run goes to the window of g consecutive CTAs that becomes free first
+// (biggest groups first), so the runs that share a CTA are ordered by their
+// start on every CTA alike and no group waits on a group that waits on it.
+tdm_status build_coop(WorkList* w, tdm_plan_s* const* ps, int count, const void* const* F, const int64_t* ldF,
+                      void* const* X, const int64_t* ldX, const int64_t* N, cudaStream_t s) {
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> by_shape;
+  for (int k = 0; k < count; k++) {
+    if (N[k] == 0) continue;
+    if (ldF[k] > kRefMaxLd || ldX[k] > kRefMaxLd) return TDM_ERR_NOT_IMPLEMENTED;
+    RefShape sh;
+    if (!tdm_refined_shape(ps[k]->M, ps[k]->t, ps[k]->tile_rhs, sh)) return TDM_ERR_NOT_IMPLEMENTED;
+    by_shape[std::make_tuple(ps[k]->t, sh.R, sh.NT, sh.sm_coef ? 1 : 0)].push_back(k);
+  }
+  std::vector<RefItem> items;
+  std::vector<RefRun> runs;
+  std::vector<int> rlist, rstart;
+  struct Pending {
+    GroupedLaunch gl;
+    size_t items0, runs0, rlist0, rstart0, scr_floats, ctr0;
+  };
+  std::vector<Pending> pend;
+  size_t scr_total = 0, ctr_total = 0;
+  for (auto& kv : by_shape) {
+    const int t = std::get<0>(kv.first), R = std::get<1>(kv.first);
+    RefShape lsh;
+    tdm_refined_shape(ps[kv.second[0]]->M, t, ps[kv.second[0]]->tile_rhs, lsh);
+    lsh.threads = lsh.NT;
+    const int P = tdm_refined_coop_runs_grid(lsh, t);
+    if (P < 16) return TDM_ERR_NOT_IMPLEMENTED;
+    struct S {
+      int k, g, tiles, item0;
+    };
+    std::vector<S> ser;
+    const size_t items0 = items.size();
+    int64_t work = 0;
+    for (int k : kv.second) {
+      RefShape sh;
+      tdm_refined_shape(ps[k]->M, t, ps[k]->tile_rhs, sh);
+      RefItem it = tdm_refined_item(ps[k], static_cast<const float*>(F[k]), ldF[k], static_cast<double*>(X[k]),
+                                    ldX[k], N[k], k, sh);
+      const int tiles = (int)((N[k] + R - 1) / R);
+      ser.push_back({k, sh.C, tiles, (int)(items.size() - items0)});
+      for (int tile = 0; tile < tiles; tile++) {
+        it.tile = tile;
+        items.push_back(it);
+      }
+      work += (int64_t)tiles * sh.C;
+    }
+    std::stable_sort(ser.begin(), ser.end(), [](const S& a, const S& b) {
+      if (a.g != b.g) return a.g > b.g;
+      return a.tiles > b.tiles;
+    });
+    const int64_t target = (work + P - 1) / P;
+    const int run_cap = (int)std::max<int64_t>(1, (target + 7) / 8);
+    std::vector<int64_t> cursor(P, 0);
+    struct Placed {
+      int64_t start;
+      int run;
+    };
+    std::vector<std::vector<Placed>> per_cta(P);
+    const size_t runs0 = runs.size();
+    for (const S& e : ser) {
+      int done = 0;
+      while (done < e.tiles) {
+        int best_p = 0;
+        int64_t best = INT64_MAX;
+        for (int p0 = 0; p0 + e.g <= P; p0++) {
+          int64_t st = 0;
+          for (int j = 0; j < e.g; j++) st = std::max(st, cursor[p0 + j]);
+          if (st < best) {
+            best = st;
+            best_p = p0;
+          }
+        }
+        int64_t len = std::min<int64_t>(e.tiles - done, run_cap);
+        if (best < target) len = std::min<int64_t>(len, std::max<int64_t>(1, target - best));
+        const int rid = (int)(runs.size() - runs0);
+        runs.push_back({e.item0 + done, (int)len, best_p, e.g});
+        for (int j = 0; j < e.g; j++) {
+          cursor[best_p + j] = best + len;
+          per_cta[best_p + j].push_back({best, rid});
+        }
+        done += (int)len;
+      }
+    }
+    const size_t rlist0 = rlist.size(), rstart0 = rstart.size();
+    for (int q = 0; q < P; q++) {
+      std::stable_sort(per_cta[q].begin(), per_cta[q].end(),
+                       [](const Placed& a, const Placed& b) { return a.start < b.start; });
+      rstart.push_back((int)(rlist.size() - rlist0));
+      for (const Placed& pl : per_cta[q]) rlist.push_back(pl.run);
+    }
+    rstart.push_back((int)(rlist.size() - rlist0));
+    GroupedLaunch gl;
+    gl.sh = lsh;
+    gl.t = t;
+    gl.coop = true;
+    gl.nclusters = P;
+    gl.nruns = (int)(runs.size() - runs0);
+    const size_t scr_floats = tdm_refined_coop_scratch(lsh, P) / sizeof(float);
+    pend.push_back({gl, items0, runs0, rlist0, rstart0, scr_floats, ctr_total});
+    scr_total += scr_floats;
+    ctr_total += (size_t)32 * gl.nruns;
+  }
+  if (items.empty()) return TDM_OK;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_items = sizeof(RefItem) * items.size(), b_runs = sizeof(RefRun) * runs.size();
+  const size_t b_rlist = sizeof(int) * rlist.size(), b_rstart = sizeof(int) * rstart.size();
+  const size_t o_runs = up(b_items), o_rlist = o_runs + up(b_runs), o_rstart = o_rlist + up(b_rlist);
+  const size_t o_scr = o_rstart + up(b_rstart), o_ctr = o_scr + up(sizeof(float) * scr_total);
+  const size_t upload = o_scr, bytes = o_ctr + sizeof(unsigned) * ctr_total;
+  TDM_CUDA_TRY(cudaMalloc(&w->d_buf, bytes));
+  TDM_CUDA_TRY(cudaMallocHost(&w->h_buf, upload));
+  memcpy(w->h_buf, items.data(), b_items);
+  memcpy(w->h_buf + o_runs, runs.data(), b_runs);
+  memcpy(w->h_buf + o_rlist, rlist.data(), b_rlist);
+  memcpy(w->h_buf + o_rstart, rstart.data(), b_rstart);
+  size_t scr_at = o_scr;
+  for (Pending& pd : pend) {
+    pd.gl.items_off = sizeof(RefItem) * pd.items0;
+    pd.gl.runs_off = o_runs + sizeof(RefRun) * pd.runs0;
+    pd.gl.units_off = o_rlist + sizeof(int) * pd.rlist0;
+    pd.gl.ustart_off = o_rstart + sizeof(int) * pd.rstart0;
+    pd.gl.scr_off = scr_at;
+    scr_at += sizeof(float) * pd.scr_floats;
+    pd.gl.ctr_off = o_ctr + sizeof(unsigned) * pd.ctr0;
+    w->launches.push_back(pd.gl);
+  }
+  TDM_CUDA_TRY(cudaMemcpyAsync(w->d_buf, w->h_buf, upload, cudaMemcpyHostToDevice, s));
+  return TDM_OK;
+}
+
 }  // namespace
 
 tdm_status tdm_set_batched_strategy(int strategy) {
-  if (strategy < 0 || strategy > 3) return TDM_ERR_INVALID_ARG;
+  if (strategy < 0 || strategy > 4) return TDM_ERR_INVALID_ARG;
   g_strategy.store(strategy);
   return TDM_OK;
 }
@@ -413,7 +556,8 @@ tdm_status tdm_launch_batched(tdm_plan_s* const* ps, int count, const void* cons
     w->key = key;
     w->device = dev;
     w->strategy = strategy;
-    tdm_status st = build(w, ps, count, F, ldF, X, ldX, N, s);
+    tdm_status st = strategy == 4 ? build_coop(w, ps, count, F, ldF, X, ldX, N, s)
+                                  : build(w, ps, count, F, ldF, X, ldX, N, s);
     if (st != TDM_OK) {
       delete w;
       return st;
@@ -421,7 +565,7 @@ tdm_status tdm_launch_batched(tdm_plan_s* const* ps, int count, const void* cons
     g_cache.push_front(w);
   }
   const int nl = (int)w->launches.size();
-  Helpers* hp = nl > 1 ? helpers_of(dev) : nullptr;
+  Helpers* hp = nl > 1 && strategy != 4 ? helpers_of(dev) : nullptr;
   const int nstreams = hp ? 1 + Helpers::kStreams : 1;
   if (hp) {   // fork
     TDM_CUDA_TRY(cudaEventRecord(hp->fork, s));
@@ -432,7 +576,13 @@ tdm_status tdm_launch_batched(tdm_plan_s* const* ps, int count, const void* cons
     const GroupedLaunch& gl = w->launches[i];
     cudaStream_t ls = (i % nstreams) == 0 ? s : hp->st[(i % nstreams) - 1];
     const RefItem* items = reinterpret_cast<const RefItem*>(w->d_buf + gl.items_off);
-    if (gl.grouped)
+    if (gl.coop)   // a cooperative grid takes the whole GPU: on the caller's stream, in order
+      st = tdm_refined_launch_coop_runs(gl.sh, gl.t, items, reinterpret_cast<const RefRun*>(w->d_buf + gl.runs_off),
+                                        reinterpret_cast<const int*>(w->d_buf + gl.units_off),
+                                        reinterpret_cast<const int*>(w->d_buf + gl.ustart_off), gl.nruns, gl.nclusters,
+                                        reinterpret_cast<float*>(w->d_buf + gl.scr_off),
+                                        reinterpret_cast<unsigned*>(w->d_buf + gl.ctr_off), ps[0]->dev_err, s);
+    else if (gl.grouped)
       st = tdm_refined_launch_grouped(gl.sh, gl.t, items, reinterpret_cast<const int*>(w->d_buf + gl.units_off),
                                       reinterpret_cast<const int*>(w->d_buf + gl.ustart_off), gl.nclusters,
                                       ps[0]->dev_err, ls);

@@ -125,6 +125,7 @@ struct Link {
   __device__ void arrive() {
     if constexpr (COOP) {
       __syncthreads();
+      if (g == 1) return;   // no peer: the CTA barrier orders its own scratch
       if (threadIdx.x == 0) {
         __threadfence();
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
@@ -136,6 +137,10 @@ struct Link {
   }
   __device__ void wait() {
     if constexpr (COOP) {
+      if (g == 1) {
+        __syncthreads();
+        return;
+      }
       if (threadIdx.x == 0 && !broken) {
         const unsigned target = narr * g;
         for (int it = 0;; it++) {
@@ -578,8 +583,10 @@ enum { kFixed = 0, kSpec = 1, kTested = 2, kRetry = 3, kCalib = 4, kRetryFixed =
 // unit, every CTA of the cluster on it (items of one cluster width, each with
 // its own blocks per CTA); grouped units (an item per CTA); one series in a
 // cooperative launch without clusters (groups of C consecutive CTAs take the
-// place of clusters, see Link).
-enum { kLaunchSingle = 0, kLaunchList = 1, kLaunchGrouped = 2, kLaunchCoop = 3 };
+// place of clusters, see Link); runs of a cooperative launch (every CTA walks
+// its own list of runs, each a range of tiles of one series on a group of
+// consecutive CTAs with a barrier counter of its own).
+enum { kLaunchSingle = 0, kLaunchList = 1, kLaunchGrouped = 2, kLaunchCoop = 3, kLaunchCoopRuns = 4 };
 
 template <int R, int TT, int NT, int MINB, bool SM, int LM>
 __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
@@ -598,7 +605,8 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   float* const eLh = eFl + MM * R;
   float* const eLl = eLh + MM * R;
   float* const red = reinterpret_cast<float*>(smem_raw + O.red);     // [2][warps][R] per-warp maxima
-  constexpr bool coop = LM == kLaunchCoop;
+  constexpr bool runs = LM == kLaunchCoopRuns;
+  constexpr bool coop = LM == kLaunchCoop || runs;
   constexpr bool one_series = LM == kLaunchSingle || LM == kLaunchCoop;
   constexpr bool grouped = LM == kLaunchGrouped;
   // what the peers read: shared memory, or this CTA's scratch block (coop)
@@ -613,8 +621,8 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   const int tid = threadIdx.x;
   const int r = tid % R;
   const int bl = tid / R;
-  const int CL = L.C;                          // CTAs per cluster, or per group (coop)
-  const unsigned cphys = coop ? blockIdx.x % CL : cluster_rank();
+  int CL = L.C;                                // CTAs per cluster, or per group (coop; runs: per run)
+  unsigned cphys = coop ? blockIdx.x % CL : cluster_rank();
   const int cluster_id = blockIdx.x / CL;
   const int nclusters = gridDim.x / CL;
   Link<coop> lk;
@@ -633,7 +641,8 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
 
 #define ITEMX(i, fld) (one_series ? L.one.fld : L.items[i].fld)
   // the item this CTA works on in unit u, and the first rank of its group
-  auto item_of = [&](int u) -> int { return grouped ? L.units[u * kUnitW + cphys] : u; };
+  int item0 = 0;   // runs: the item of the run's first tile
+  auto item_of = [&](int u) -> int { return grouped ? L.units[u * kUnitW + cphys] : runs ? item0 + u : u; };
   auto group_base = [&](int gs) -> unsigned { return grouped ? (cphys & ~(unsigned)(gs - 1)) : 0u; };
   // largest ratio over the groups (every CTA the same) and this CTA's group's
   auto ratios = [&](const float* slot, float& own) -> float {
@@ -662,12 +671,34 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
   int parity = 0;
   int preloaded = -1;       // the unit whose F g holds (loaded during the previous output)
   int u_next = grouped ? L.ustart[cluster_id] : cluster_id;
-  const int u_end = grouped ? L.ustart[cluster_id + 1] : L.nitems;
-  const int u_step = grouped ? 1 : nclusters;
+  int u_end = grouped ? L.ustart[cluster_id + 1] : L.nitems;
+  const int u_step = grouped || runs ? 1 : nclusters;
   int pending = -1;         // a speculative unit that failed its verification
   int unverified = -1;      // the last speculative unit, its maxima not checked yet
   int vslot = 0;            // and its verification slot
   int nspec = 0;            // speculative units so far (slot rotation)
+  const int run_end = runs ? L.ustart[blockIdx.x + 1] : 1;
+  for (int run_i = runs ? L.ustart[blockIdx.x] : 0; run_i < run_end; run_i++) {
+  if constexpr (runs) {   // a new run: its group, its counter, its tiles; the exchange state starts afresh
+    const int rid = L.units[run_i];
+    const RefRun rn = L.runs[rid];
+    item0 = rn.item0;
+    CL = rn.g;
+    cphys = blockIdx.x - (unsigned)rn.first;
+    lk.first = (unsigned)rn.first;
+    lk.g = (unsigned)rn.g;
+    lk.ctr = L.ctr + 32 * (size_t)rid;
+    lk.narr = 0;
+    u_next = 0;
+    u_end = rn.ntiles;
+    parity = 0;
+    preloaded = -1;
+    pending = -1;
+    unverified = -1;
+    nspec = 0;
+    // the previous run's peers are done with this CTA's slots (closing barrier)
+    for (int k = tid; k < kVerSlots * SL; k += blockDim.x) ver[k] = 0.f;
+  }
   while (true) {
     int u;
     bool retry = false;
@@ -964,6 +995,8 @@ __global__ void __launch_bounds__(NT, MINB) k_refined(const RefLaunch L) {
 #undef ITEMV
 #undef ITEM
   }
+  if constexpr (runs) lk.barrier();   // closing: no peer of the run reads this CTA's slots any more
+  }
 #undef ITEMX
   // no CTA may leave while a peer can still read its shared memory (the
   // scratch blocks of a cooperative launch stay readable)
@@ -1206,6 +1239,64 @@ tdm_status tdm_refined_launch_coop(const RefShape& sh, int t, const RefItem& one
         at[0].id = cudaLaunchAttributeCooperative;
         at[0].val.cooperative = 1;
         lc.gridDim = dim3(groups * sh.C);
+        lc.blockDim = dim3(sh.threads);
+        lc.dynamicSmemBytes = sh.smem;
+        lc.stream = s;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        if (cudaLaunchKernelEx(&lc, kern, L) != cudaSuccess) st = TDM_ERR_CUDA;
+      }))
+    return TDM_ERR_NOT_IMPLEMENTED;
+  return st;
+}
+
+int tdm_refined_coop_runs_grid(const RefShape& sh, int t) {
+  int grid = 0;
+  with_shape(sh, t, [&](auto tag) {
+    using S = decltype(tag);
+    auto kern = refined_kernel<S, kLaunchCoopRuns>();
+    int dev = 0, sms = 0, nb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, sh.threads, sh.smem) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return;
+    }
+    grid = nb * sms;
+  });
+  return grid;
+}
+
+tdm_status tdm_refined_launch_coop_runs(const RefShape& sh, int t, const RefItem* items, const RefRun* runs,
+                                        const int* rlist, const int* rstart, int nruns, int grid, float* scr,
+                                        unsigned* ctr, int* err, cudaStream_t s) {
+  if (nruns <= 0 || grid <= 0) return TDM_OK;
+  RefLaunch L;
+  memset(&L, 0, sizeof(L));
+  L.items = items;
+  L.units = rlist;
+  L.ustart = rstart;
+  L.runs = runs;
+  L.single = 0;
+  L.m = sh.m;
+  L.C = 1;
+  L.err = err;
+  L.scr = scr;
+  L.ctr = ctr;
+  TDM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned) * 32 * (size_t)nruns, s));
+  tdm_status st = TDM_OK;
+  if (!with_shape(sh, t, [&](auto tag) {
+        using S = decltype(tag);
+        auto kern = refined_kernel<S, kLaunchCoopRuns>();
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess) {
+          st = TDM_ERR_CUDA;
+          return;
+        }
+        cudaLaunchConfig_t lc = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        lc.gridDim = dim3(grid);
         lc.blockDim = dim3(sh.threads);
         lc.dynamicSmemBytes = sh.smem;
         lc.stream = s;

@@ -57,10 +57,18 @@ struct RefItem {
 // ustart[k] .. ustart[k + 1] - 1 in order.
 constexpr int kUnitW = 16;
 
+// A run of a cooperative batched launch: tiles item0 .. item0 + ntiles - 1 (of
+// one series) on the CTAs first .. first + g - 1; its barrier counter is the
+// run's index.
+struct RefRun {
+  int item0, ntiles, first, g;
+};
+
 struct RefLaunch {
   const RefItem* items;   // work list (device); unused when single
-  const int* units;       // grouped: [units][kUnitW] item of every CTA; null otherwise
-  const int* ustart;      // grouped: [clusters + 1] first unit of every cluster
+  const int* units;       // grouped: [units][kUnitW] item of every CTA; runs: the run ids of every CTA, in order
+  const int* ustart;      // grouped: [clusters + 1] first unit of every cluster; runs: [CTAs + 1] into units
+  const RefRun* runs;     // runs: the runs
   RefItem one;            // the series of a single-series launch (item i = its tile i)
   int nitems;             // single: tiles; list: items (cluster k takes k, k + clusters, ...)
   int single;
@@ -98,6 +106,14 @@ tdm_status tdm_refined_launch_grouped(const RefShape& sh, int t, const RefItem* 
                                       const int* ustart, int nclusters, int* err, cudaStream_t s);
 // clusters of sh.C CTAs of the shape's kernel that the device holds at once
 int tdm_refined_max_clusters(const RefShape& sh, int t);
+// A cooperative launch over runs (sh: the kernel's shape; grid CTAs): CTA b
+// walks the runs rlist[rstart[b]] .. rlist[rstart[b + 1] - 1]; the nruns
+// counters ctr[32 * id] are zeroed on the stream first; scr holds grid
+// scratch blocks (tdm_refined_coop_scratch).
+int tdm_refined_coop_runs_grid(const RefShape& sh, int t);
+tdm_status tdm_refined_launch_coop_runs(const RefShape& sh, int t, const RefItem* items, const RefRun* runs,
+                                        const int* rlist, const int* rstart, int nruns, int grid, float* scr,
+                                        unsigned* ctr, int* err, cudaStream_t s);
 // Cooperative launches of one series (groups of sh.C consecutive CTAs in
 // place of clusters): the largest grid of whole groups the device holds at
 // once (0 if none), the bytes of scratch that grid needs, and the launch (its

@@ -112,14 +112,15 @@ def test_batched_other_precisions(tdm, dev, oracle, precision):
         p.close()
 
 
-@pytest.fixture
-def grouped(tdm):
-    tdm.set_batched_strategy("grouped")
-    yield
+@pytest.fixture(params=["grouped", "cooperative"])
+def grouped(tdm, request):
+    """The layouts in which tiles of several series share one launch."""
+    tdm.set_batched_strategy(request.param)
+    yield request.param
     tdm.set_batched_strategy("auto")
 
 
-@pytest.mark.parametrize("strategy", ["per_series", "by_width", "grouped"])
+@pytest.mark.parametrize("strategy", ["per_series", "by_width", "grouped", "cooperative"])
 def test_batched_strategies_match_single_solves(tdm, dev, oracle, strategy):
     """Both layouts of the batched work give every series the result of its own
     solve, bit for bit, over sizes that need clusters of 1 to 16 CTAs and
@@ -151,10 +152,12 @@ def test_batched_strategies_match_single_solves(tdm, dev, oracle, strategy):
 
 def test_grouped_launch_mixed_schedules(tdm, dev, oracle, grouped):
     """Plans of three correction schedules in one call -- the calibrated
-    per-tile test, two fixed corrections, the uncalibrated test -- each in a
-    grouped launch of its own.  The first two equal the plan's own solve bit
-    for bit (a series keeps its single-series partition inside its group); the
-    third runs the fixed retry count; all meet the gate."""
+    per-tile test, two fixed corrections, the uncalibrated test.  Grouped
+    units put each schedule in a launch of its own; the first two equal the
+    plan's own solve bit for bit (a series keeps its single-series partition
+    inside its group), the third runs the fixed retry count.  Cooperative runs
+    mix them in one launch and all three equal the plan's own solve.  All meet
+    the gate."""
     series = _batch(seed=5, count=18, n_min=100, n_max=9000, N_max=50)
     steps = [0, 2, -1] * 6
     plans = [tdm.prepare(s.a, s.b, refine_steps=k, device=dev) for s, k in zip(series, steps)]
@@ -163,7 +166,7 @@ def test_grouped_launch_mixed_schedules(tdm, dev, oracle, grouped):
     Xs = [p.solve(F, "fp32_refined") for p, F in zip(plans, Fs)]
     torch.cuda.synchronize()
     for s, k, xb, xs in zip(series, steps, Xb, Xs):
-        if k != -1:
+        if k != -1 or grouped == "cooperative":
             assert torch.equal(xb, xs), (s.n, k)
         ref = oracle.solve_hi(s.a, s.b, s.F.astype(np.float64))
         assert relerr(xb.cpu().numpy(), ref) <= 1e-11, (s.n, k)
@@ -210,7 +213,8 @@ def test_grouped_launch_retries_a_failing_unit(tdm, dev, oracle, grouped):
         p.close()
 
 
-def test_batching_workload_sampled_against_the_oracle(tdm, dev, oracle):
+@pytest.mark.parametrize("strategy", ["auto", "cooperative"])
+def test_batching_workload_sampled_against_the_oracle(tdm, dev, oracle, strategy):
     """The full batching workload (512 Fourier-mode matrices of lognormal size
     up to n = 43943, 1.7e9 unknowns, F ~ N(0,1) drawn on the device) in one
     call, as the benchmark runs it; sampled columns of 16 matrices (the three
@@ -221,7 +225,11 @@ def test_batching_workload_sampled_against_the_oracle(tdm, dev, oracle):
     gen.manual_seed(1234)
     plans = [tdm.prepare(s.a, s.b, device=dev) for s in specs]
     Fs = [torch.randn((s.n, s.meta["N"]), device=dev, dtype=torch.float32, generator=gen) for s in specs]
-    Xs = tdm.solve_batched(plans, Fs, "fp32_refined")
+    tdm.set_batched_strategy(strategy)
+    try:
+        Xs = tdm.solve_batched(plans, Fs, "fp32_refined")
+    finally:
+        tdm.set_batched_strategy("auto")
     torch.cuda.synchronize()
     order = np.argsort([s.n for s in specs])
     rng = np.random.default_rng(7)
