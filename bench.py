@@ -258,7 +258,8 @@ def run_gpu(args):
                                  "during the next tile; a failing tile is solved again with more",
                    "block_rows": info["block_rows"],
                    "parallelism": f"rhs-sharded x{DIST['world']}" if DIST["world"] > 1 else "single GPU",
-                   "l2": "no flush: F (512 MiB) and X (1 GiB) exceed L2"},
+                   "l2": f"no flush: F ({N_ROWS * N_RHS * 4 >> 20} MiB) and X ({N_ROWS * N_RHS * 8 >> 20} MiB) "
+                         "exceed L2" if N_ROWS * N_RHS * 4 > (129 << 20) else "no flush: a sample smaller than L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
                      "kernel": "k_refined", "algorithmic_bytes_per_launch": bytes_refined},
