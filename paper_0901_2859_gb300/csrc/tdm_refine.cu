@@ -77,99 +77,6 @@ constexpr float kRefineTol = 1e-12f;
 constexpr float kRefineTol1 = 4e-12f;
 constexpr int kRefineCap = 4;
 
-// The peers of a tile and their barrier.
-//  * Cluster (COOP false): the CTAs of the thread-block cluster.  Barriers are
-//    the hardware cluster barrier; what the peers read sits in shared memory
-//    and is read through the cluster's shared-memory window.
-//  * Group (COOP true): g consecutive CTAs of a cooperative launch (every CTA
-//    of the grid resident at once).  A barrier is a counter in global memory:
-//    each CTA, after its writes, adds 1 with release semantics, and waits
-//    until the count reaches its own arrivals times g (a bounded spin by one
-//    thread; on time-out it records kDevErrGroupTimeout and stops waiting).
-//    What the peers read sits in a scratch block of kScr floats per CTA in
-//    global memory, read with gpu-scope loads (not through L1) after the
-//    barrier.  Ranks are group-relative: rank k is the CTA first + k.
-constexpr int kGroupSpinLimit = 1 << 21;
-template <bool COOP>
-struct Link {
-  unsigned me = 0;         // this CTA's index in the grid (COOP)
-  unsigned first = 0;      // the grid index of the group's rank 0 (COOP)
-  int stride = 0;          // floats between consecutive CTAs' scratch blocks (COOP)
-  unsigned g = 0;          // CTAs of the group (COOP)
-  unsigned* ctr = nullptr; // the group's counter (COOP)
-  int* err = nullptr;
-  unsigned narr = 0;       // this CTA's arrivals so far
-  bool broken = false;     // a wait timed out (thread 0)
-  __device__ const float* at(const float* mine, unsigned rank) const {
-    return mine + ((int)(first + rank) - (int)me) * stride;
-  }
-  __device__ float ld(const float* mine, unsigned rank) const {
-    if constexpr (COOP) {
-      float v;
-      asm volatile("ld.relaxed.gpu.f32 %0, [%1];" : "=f"(v) : "l"(at(mine, rank)) : "memory");
-      return v;
-    } else {
-      return ld_cluster_f32(mine, rank);
-    }
-  }
-  __device__ float2 ld2(const float2* mine, unsigned rank) const {
-    if constexpr (COOP) {
-      const float* p = at(reinterpret_cast<const float*>(mine), rank);
-      float2 v;
-      asm volatile("ld.relaxed.gpu.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
-      return v;
-    } else {
-      return ld_cluster_f32x2(mine, rank);
-    }
-  }
-  __device__ void arrive() {
-    if constexpr (COOP) {
-      __syncthreads();
-      if (g == 1) return;   // no peer: the CTA barrier orders its own scratch
-      if (threadIdx.x == 0) {
-        __threadfence();
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
-      }
-      narr++;
-    } else {
-      cluster_arrive();
-    }
-  }
-  __device__ void wait() {
-    if constexpr (COOP) {
-      if (g == 1) {
-        __syncthreads();
-        return;
-      }
-      if (threadIdx.x == 0 && !broken) {
-        const unsigned target = narr * g;
-        for (int it = 0;; it++) {
-          unsigned v;
-          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
-          if (v >= target) break;
-          if (it >= kGroupSpinLimit) {
-            broken = true;
-            atomicExch(err, kDevErrGroupTimeout);
-            break;
-          }
-          if (it >= 32) __nanosleep(64);
-        }
-      }
-      __syncthreads();
-    } else {
-      cluster_wait();
-    }
-  }
-  __device__ void barrier() {
-    if constexpr (COOP) {
-      arrive();
-      wait();
-    } else {
-      cluster_barrier();
-    }
-  }
-};
-
 // Scratch block of a CTA of a cooperative launch (floats): the A4 totals
 // [2 parity][2 dir][R] pairs, the edge rows of x (first block: high, low;
 // last block: high, low) [4][R], the correction maxima [4][kSlot], the
