@@ -64,3 +64,43 @@ def test_requested_tile_widths_agree(tile, oracle):
     torch.cuda.synchronize()
     assert relerr(X.cpu().numpy(), oracle.solve_hi(s.a, s.b, s.F.astype(np.float64))) <= 1e-11
     plan.close()
+
+
+def test_size_classes_are_octaves():
+    from paper_0901_2859_gb300.autotune import size_class
+    assert [size_class(n) for n in (1, 2, 3, 1023, 1024, 2047, 16384)] == [0, 1, 1, 9, 10, 10, 14]
+
+
+@pytest.mark.gpu
+def test_batch_tuning_per_size_class_and_layout(tmp_path, monkeypatch, oracle):
+    """A batch of 12 matrices over three octaves: one tile width tuned per
+    class on its largest matrix, the plans built with them, the batched layouts
+    timed on the batch and the fastest selected and cached; the tuned batch
+    meets the gate against the oracle."""
+    import torch
+    import paper_0901_2859_gb300 as tdm
+    from paper_0901_2859_gb300 import autotune, workloads
+    monkeypatch.setenv("TDM_TUNE_CACHE", str(tmp_path / "tune.json"))
+    dev = torch.device("cuda", 0)
+    specs = workloads.batching(seed=3, count=12, K=12, n_median=2000, n_min=700, n_max=6000, N_max=60)
+    pairs = [(s.a, s.b) for s in specs]
+    tiles = autotune.tune_size_classes(pairs, device=dev, sample_rhs=64, reps=2)
+    assert set(tiles) == {autotune.size_class(len(b)) for _, b in pairs}
+    assert all(t in (4, 8, 16) for t in tiles.values())
+    plans = autotune.prepare_batch(pairs, device=dev, sample_rhs=64, reps=2)
+    assert [p.info()["tile_rhs"] for p in plans] == [tiles[autotune.size_class(p.n)] for p in plans]
+    Fs = [torch.from_numpy(s.F).to(dev) for s in specs]
+    outs = [torch.empty((p.n, F.shape[1]), dtype=torch.float64, device=dev) for p, F in zip(plans, Fs)]
+    try:
+        choice = autotune.tune_layout(plans, Fs, outs, reps=2)
+        assert choice["layout"] in autotune.LAYOUTS and len(choice["layouts"]) == len(autotune.LAYOUTS)
+        cached = json.loads((tmp_path / "tune.json").read_text())
+        assert any(v.get("layout") == choice["layout"] for v in cached.values())
+        tdm.solve_batched(plans, Fs, "fp32_refined", outs=outs)
+        torch.cuda.synchronize()
+    finally:
+        tdm.set_batched_strategy("auto")
+    for s, x in zip(specs, outs):
+        assert relerr(x.cpu().numpy(), oracle.solve_hi(s.a, s.b, s.F.astype(np.float64))) <= 1e-11
+    for p in plans:
+        p.close()
