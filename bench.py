@@ -238,6 +238,14 @@ def run_gpu(args):
 
     ke = max(3, min(args.steps, 20))
     ms_e2e = _max_over_ranks(_events_time(e2e_step, ke, 2, torch), torch)
+    # the host link's own rate (contiguous pinned copies of 256 MiB each way), outside the timed region:
+    # the end-to-end ceiling is the slower direction's bytes over its rate
+    hb = torch.empty(256 << 20, dtype=torch.uint8).pin_memory()
+    db = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    link_h2d = (256 << 20) / (_events_time(lambda: db.copy_(hb, non_blocking=True), 3, 2, torch) * 1e-3) / 1e9
+    link_d2h = (256 << 20) / (_events_time(lambda: hb.copy_(db, non_blocking=True), 3, 2, torch) * 1e-3) / 1e9
+    del hb, db
+    ceiling_ms = max(unknowns * 4 / link_h2d, unknowns * 8 / link_d2h) / 1e6
 
     # the refined solution of a few columns, for the accuracy check of the baseline leg
     plan.solve(F, "fp32_refined", out=X)
@@ -264,7 +272,9 @@ def run_gpu(args):
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
                      "kernel": "k_refined", "algorithmic_bytes_per_launch": bytes_refined},
         "e2e": {"value": DIST["world"] * unknowns / (ms_e2e * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": unknowns * 4, "d2h_bytes_per_step": unknowns * 8},
+                "h2d_bytes_per_step": unknowns * 4, "d2h_bytes_per_step": unknowns * 8, "ms_per_step": ms_e2e,
+                "link_gbs": {"h2d": link_h2d, "d2h": link_d2h},
+                "link_ceiling": {"value": DIST["world"] * unknowns / (ceiling_ms * 1e-3), "ms_per_step": ceiling_ms}},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "paths": {
