@@ -170,9 +170,10 @@ tdm_status tdm_prepare_general(const double* sub, const double* diag, const doub
  * symmetric plan is solved in two levels (Lemma 1 one level up): segments of
  * at most 1024 * block_rows rows, each by a plan of its own, and the values at
  * the rows between them from a reduced tridiagonal plan; X then takes one more
- * read and write.  Batched refined solves (tdm_solve_batched with
- * TDM_FP32_REFINED, tdm_solve_batched_noalloc) of such plans and general plans
- * beyond the limit return TDM_ERR_NOT_IMPLEMENTED.
+ * read and write.  tdm_solve_batched solves such plans by their two-level
+ * solve, one after the other on the stream, beside the batched layout of the
+ * others; tdm_solve_batched_noalloc (whose two-level solve would allocate)
+ * and general plans beyond the limit return TDM_ERR_NOT_IMPLEMENTED.
  * Errors: TDM_ERR_INVALID_ARG, TDM_ERR_NOT_IMPLEMENTED, TDM_ERR_CUDA. */
 tdm_status tdm_solve(tdm_handle h, const void* F, int64_t ldF, void* X, int64_t ldX,
                      int64_t N, tdm_precision prec, void* stream);

@@ -487,6 +487,9 @@ tdm_status tdm_set_batched_strategy(int strategy) {
   return TDM_OK;
 }
 
+static tdm_status launch_batched_refined(tdm_plan_s* const* ps, int count, const void* const* F, const int64_t* ldF,
+                                        void* const* X, const int64_t* ldX, const int64_t* N, cudaStream_t s);
+
 tdm_status tdm_launch_batched(tdm_plan_s* const* ps, int count, const void* const* F, const int64_t* ldF,
                               void* const* X, const int64_t* ldX, const int64_t* N, tdm_precision prec,
                               cudaStream_t s) {
@@ -498,6 +501,34 @@ tdm_status tdm_launch_batched(tdm_plan_s* const* ps, int count, const void* cons
     }
     return TDM_OK;
   }
+  // Series beyond one cluster (two-level plans) are solved one after the
+  // other by their own two-level solve; the others share the batched layout.
+  std::vector<tdm_plan_s*> ps1;
+  std::vector<const void*> F1;
+  std::vector<void*> X1;
+  std::vector<int64_t> ldF1, ldX1, N1;
+  for (int k = 0; k < count; k++) {
+    if (N[k] > 0 && ps[k]->nseg > 0) continue;
+    ps1.push_back(ps[k]);
+    F1.push_back(F[k]);
+    X1.push_back(X[k]);
+    ldF1.push_back(ldF[k]);
+    ldX1.push_back(ldX[k]);
+    N1.push_back(N[k]);
+  }
+  if ((int)ps1.size() < count) {
+    tdm_status st = ps1.empty() ? TDM_OK
+                                : launch_batched_refined(ps1.data(), (int)ps1.size(), F1.data(), ldF1.data(),
+                                                         X1.data(), ldX1.data(), N1.data(), s);
+    for (int k = 0; k < count && st == TDM_OK; k++)
+      if (N[k] > 0 && ps[k]->nseg > 0) st = tdm_launch_solve(ps[k], F[k], ldF[k], X[k], ldX[k], N[k], prec, s);
+    return st;
+  }
+  return launch_batched_refined(ps, count, F, ldF, X, ldX, N, s);
+}
+
+static tdm_status launch_batched_refined(tdm_plan_s* const* ps, int count, const void* const* F, const int64_t* ldF,
+                                        void* const* X, const int64_t* ldX, const int64_t* N, cudaStream_t s) {
   int dev = 0;
   cudaGetDevice(&dev);
   int strategy = g_strategy.load();

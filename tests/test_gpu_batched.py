@@ -243,3 +243,28 @@ def test_batching_workload_sampled_against_the_oracle(tdm, dev, oracle, strategy
     assert all(p.info()["device_error"] == 0 for p in plans)
     for p in plans:
         p.close()
+
+
+def test_batched_refined_with_a_plan_beyond_one_cluster(tdm, dev, oracle):
+    """A batch whose largest series (n = 70001) needs the two-level solve: it is
+    solved by that solve inside the same call, the others by the batched layout;
+    everything meets the gate and equals the series' own solves."""
+    from paper_0901_2859_gb300 import workloads
+    sizes = [(70001, 6), (3000, 20), (900, 9)]
+    series = []
+    for m, (n, N) in enumerate(sizes):
+        rng = np.random.default_rng(70 + m)
+        sh = 4.0 * np.sin(np.pi * (m + 1) / (2.0 * 65)) ** 2
+        series.append(workloads.Series(-np.ones(n - 1), np.full(n, 2.0 + sh),
+                                       rng.standard_normal((n, N), dtype=np.float32)))
+    plans, Fs = _upload(tdm, dev, series)
+    Xb = tdm.solve_batched(plans, Fs, "fp32_refined")
+    Xs = [p.solve(F, "fp32_refined") for p, F in zip(plans, Fs)]
+    torch.cuda.synchronize()
+    for s, xb, xs in zip(series, Xb, Xs):
+        assert torch.equal(xb, xs), s.n
+        ref = oracle.solve_hi(s.a, s.b, s.F.astype(np.float64))
+        assert relerr(xb.cpu().numpy(), ref) <= 1e-11, s.n
+    for p in plans:
+        assert p.info()["device_error"] == 0
+        p.close()
