@@ -392,7 +392,9 @@ struct ClusterPeers {
 //    and is read through the cluster's shared-memory window.
 //  * Group (COOP true): g consecutive CTAs of a cooperative launch (every CTA
 //    of the grid resident at once).  A barrier is a counter in global memory:
-//    each CTA, after its writes, adds 1 with release semantics, and waits
+//    each CTA, after its writes and a CTA barrier, adds 1 from one thread with
+//    release semantics (the barrier orders the other threads' writes before
+//    it), and waits
 //    until the count reaches its own arrivals times g (a bounded spin by one
 //    thread; on time-out it records kDevErrGroupTimeout and stops waiting).
 //    What the peers read sits in a scratch block of kScr floats per CTA in
@@ -435,8 +437,7 @@ struct Link {
     if constexpr (COOP) {
       __syncthreads();
       if (g == 1) return;   // no peer: the CTA barrier orders its own scratch
-      if (threadIdx.x == 0) {
-        __threadfence();
+      if (threadIdx.x == 0) {   // the CTA barrier orders the other threads' writes before this release
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
       }
       narr++;
