@@ -238,14 +238,30 @@ def run_gpu(args):
 
     ke = max(3, min(args.steps, 20))
     ms_e2e = _max_over_ranks(_events_time(e2e_step, ke, 2, torch), torch)
-    # the host link's own rate (contiguous pinned copies of 256 MiB each way), outside the timed region:
-    # the end-to-end ceiling is the slower direction's bytes over its rate
+    # the host link's own rates, outside the timed region: contiguous pinned copies of 256 MiB each way, and
+    # 128 MiB in with 256 MiB out at the same time (the step's 1:2 ratio); the end-to-end ceiling is the step's
+    # bytes at the simultaneous rate (the link does not carry both directions at their full one-way rates)
     hb = torch.empty(256 << 20, dtype=torch.uint8).pin_memory()
     db = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    hb2 = torch.empty(128 << 20, dtype=torch.uint8).pin_memory()
+    db2 = torch.empty(128 << 20, dtype=torch.uint8, device=dev)
     link_h2d = (256 << 20) / (_events_time(lambda: db.copy_(hb, non_blocking=True), 3, 2, torch) * 1e-3) / 1e9
     link_d2h = (256 << 20) / (_events_time(lambda: hb.copy_(db, non_blocking=True), 3, 2, torch) * 1e-3) / 1e9
-    del hb, db
-    ceiling_ms = max(unknowns * 4 / link_h2d, unknowns * 8 / link_d2h) / 1e6
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def both_ways():
+        cur = torch.cuda.current_stream(dev)
+        s_in.wait_stream(cur)
+        s_out.wait_stream(cur)
+        with torch.cuda.stream(s_in):
+            db2.copy_(hb2, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            hb.copy_(db, non_blocking=True)
+        cur.wait_stream(s_in)
+        cur.wait_stream(s_out)
+    link_both = (384 << 20) / (_events_time(both_ways, 3, 2, torch) * 1e-3) / 1e9
+    del hb, db, hb2, db2
+    ceiling_ms = unknowns * 12 / link_both / 1e6
 
     # the refined solution of a few columns, for the accuracy check of the baseline leg
     plan.solve(F, "fp32_refined", out=X)
@@ -273,7 +289,7 @@ def run_gpu(args):
                      "kernel": "k_refined", "algorithmic_bytes_per_launch": bytes_refined},
         "e2e": {"value": DIST["world"] * unknowns / (ms_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": unknowns * 4, "d2h_bytes_per_step": unknowns * 8, "ms_per_step": ms_e2e,
-                "link_gbs": {"h2d": link_h2d, "d2h": link_d2h},
+                "link_gbs": {"h2d": link_h2d, "d2h": link_d2h, "both_ways_1to2": link_both},
                 "link_ceiling": {"value": DIST["world"] * unknowns / (ceiling_ms * 1e-3), "ms_per_step": ceiling_ms}},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
