@@ -536,6 +536,49 @@ def run_large(args):
         print(json.dumps(line), flush=True)
 
 
+def run_backward(args):
+    """The backward of the solve (row A8) on the differentiation workload (n = 8192,
+    N = 2048, a random dominant matrix): dF = A^{-1} W by the adjoint solve with
+    the same plan (Lemma 2) and the deterministic row reductions of da, db, in the
+    binary32 and the refined precision."""
+    import torch
+    import paper_0901_2859_gb300 as tdm
+    from paper_0901_2859_gb300 import workloads
+
+    dev = torch.device("cuda", DIST["local"])
+    torch.cuda.set_device(dev)
+    w = workloads.diff(seed=DIST["rank"])
+    n, N = w.n, w.F.shape[1]
+    plan = tdm.prepare(w.a, w.b, device=dev)
+    F = torch.from_numpy(w.F).to(dev)
+    W = torch.from_numpy(w.W).to(dev)
+    hbm, peak_kind = _peaks()
+    paths = {}
+    # bytes per unknown: W read and dF written by the adjoint solve, dF and X read by the reductions
+    for prec, x_dtype, w_in, bytes_per in (("fp32", torch.float32, W, 16), ("fp32_refined", torch.float64, W, 24)):
+        X = plan.solve(F, prec)
+        steps = max(3, min(args.steps, 20))
+        ms = _events_time(lambda: plan.solve_backward(w_in, X, prec), steps, args.warmup, torch)
+        paths[prec] = {"ms": ms, "unknowns_per_s": n * N / (ms * 1e-3), "bytes_per_unknown": bytes_per,
+                       "hbm_frac": n * N * bytes_per / (ms * 1e-3) / 1e9 / hbm}
+        del X
+    plan.close()
+    line = {
+        "metric": "unknowns/s of the backward (dF, da, db)", "value": paths["fp32"]["unknowns_per_s"], "unit": UNIT,
+        "n_gpus": DIST["world"], "steps": max(3, min(args.steps, 20)), "warmup": args.warmup,
+        "ms_per_step": paths["fp32"]["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"backward: diff n={n} N={N}, a ~ U[-1,-0.5], b ~ U[2.2,3], F, W ~ N(0,1) fp32",
+                   "n": n, "N": N},
+        "roofline": {"bound": "hbm", "achieved": n * N * 16 / (paths["fp32"]["ms"] * 1e-3) / 1e9, "peak": hbm,
+                     "unit": "GB/s", "frac": paths["fp32"]["hbm_frac"], "traffic": None, "peak_source": peak_kind,
+                     "kernel": "k_solve<float> + k_grad_rows"},
+        "paths": paths,
+    }
+    if DIST["rank"] == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_algorithm2(args):
     """Algorithm 2 (Section 3.1) at the benchmark size: every separator value of
     the precision series (P = M - 1 = 511 components) as G^T F, by the library's
@@ -640,10 +683,11 @@ def main():
     ap.add_argument("--cpu-cols", type=int, default=8192, help="columns of the CPU baseline sample")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline: seconds of repeated passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "poisson2d", "adi", "large", "algorithm2"],
-                    help="precision: the benchmark line; batching: 512 matrices of uneven size in one launch; "
+    ap.add_argument("--workload", default="precision", choices=["precision", "batching", "poisson2d", "adi", "large", "algorithm2", "backward"],
+                    help="precision: the benchmark line; batching: 512 matrices of uneven size in one call; "
                          "poisson2d: the Fourier method on a 1024 x 1024 mesh, 100 problems; adi: alternating directions; "
-                         "large: the two-level solve beyond one cluster; algorithm2: separator values as dense products")
+                         "large: the two-level solve beyond one cluster; algorithm2: separator values as dense products; "
+                         "backward: the gradient of the solve")
     ap.add_argument("--rhs", type=int, default=N_RHS,
                     help="right-hand sides of the series (the benchmark is 8192; smaller values are for profiling)")
     args = ap.parse_args()
@@ -653,6 +697,8 @@ def main():
         run_reference(args)
     elif args.workload == "algorithm2":
         run_algorithm2(args)
+    elif args.workload == "backward":
+        run_backward(args)
     elif args.workload == "large":
         run_large(args)
     elif args.workload == "adi":

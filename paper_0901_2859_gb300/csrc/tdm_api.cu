@@ -3,6 +3,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "tdm_internal.cuh"
 #include "tdm_tma.cuh"
 
@@ -94,6 +96,64 @@ __global__ void __launch_bounds__(256) k_grad_rows(const T* __restrict__ L, cons
   }
 }
 
+// The same sums for binary32 Lambda and X without binary64 arithmetic (one
+// binary64 operation costs as much issue as 64 binary32 ones on GB300): each
+// product is formed exactly as p + e (e = fma(l, x, -p)), added to a binary32
+// pair accumulator by Knuth's TwoSum with the errors gathered in the low word
+// (about 2^-44 relative to the sum of |terms| over a row of 2048 terms).  One
+// warp per row: lane k sums the right-hand sides k, k + 32, ... in order, the
+// lanes' pairs are added in a fixed butterfly, lane 0 rounds the pair to
+// binary64.  Deterministic.
+// (every operation an intrinsic with round-to-nearest, never contracted into
+// an FMA, so that TwoSum's error term is exact)
+__device__ __forceinline__ void acc_product(float l, float x, float& hi, float& lo) {
+  const float p = __fmul_rn(l, x);
+  const float e = fmaf(l, x, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+__device__ __forceinline__ void add_pair(float& hi, float& lo, float h2, float l2) {
+  const float s = __fadd_rn(hi, h2);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, l2));
+}
+__global__ void __launch_bounds__(256) k_grad_rows_f32(const float* __restrict__ L, const float* __restrict__ X,
+                                                       int64_t ld, int64_t N, int64_t n,
+                                                       double* __restrict__ da, double* __restrict__ db) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+    const bool has_next = i + 1 < n;
+    float bh = 0.f, bl = 0.f, ah = 0.f, al = 0.f;
+    const float* Li = L + i * ld;
+    const float* Xi = X + i * ld;
+    for (int64_t r = lane; r < N; r += 32) {
+      const float li = Li[r], xi = Xi[r];
+      acc_product(li, xi, bh, bl);
+      if (has_next) {
+        acc_product(li, Xi[ld + r], ah, al);
+        acc_product(Li[ld + r], xi, ah, al);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const float bh2 = __shfl_xor_sync(0xffffffffu, bh, o), bl2 = __shfl_xor_sync(0xffffffffu, bl, o);
+      const float ah2 = __shfl_xor_sync(0xffffffffu, ah, o), al2 = __shfl_xor_sync(0xffffffffu, al, o);
+      add_pair(bh, bl, bh2, bl2);
+      add_pair(ah, al, ah2, al2);
+    }
+    if (lane == 0) {
+      if (db) db[i] = -((double)bh + (double)bl);
+      if (da && has_next) da[i] = -((double)ah + (double)al);
+    }
+  }
+}
+
 // A wait on an mbarrier that no thread arrives at: the bounded wait of the
 // solve kernels, with a caller-chosen limit, must give up and report.
 __global__ void k_wait_selftest(int* err, long long limit) {
@@ -158,9 +218,9 @@ tdm_status tdm_launch_backward_sums(tdm_plan_s* p, const void* W, const void* X,
   if (prec != TDM_FP32)   // Lambda and X in binary64 (the binary64 and the refined solves)
     k_grad_rows<double><<<grid, 256, 0, s>>>(static_cast<const double*>(W), static_cast<const double*>(X),
                                              ld, N, n, da, db);
-  else
-    k_grad_rows<float><<<grid, 256, 0, s>>>(static_cast<const float*>(W), static_cast<const float*>(X),
-                                            ld, N, n, da, db);
+  else   // binary32 pairs: one warp per row
+    k_grad_rows_f32<<<(int)std::min<int64_t>((n + 7) / 8, 65536), 256, 0, s>>>(
+        static_cast<const float*>(W), static_cast<const float*>(X), ld, N, n, da, db);
   TDM_CUDA_TRY(cudaGetLastError());
   return TDM_OK;
 }
