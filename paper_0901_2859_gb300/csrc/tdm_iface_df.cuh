@@ -423,6 +423,16 @@ struct Link {
       return ld_cluster_f32(mine, rank);
     }
   }
+  __device__ double ldd(const double* mine, unsigned rank) const {
+    if constexpr (COOP) {
+      const double* p = reinterpret_cast<const double*>(at(reinterpret_cast<const float*>(mine), rank));
+      double v;
+      asm volatile("ld.relaxed.gpu.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+      return v;
+    } else {
+      return ld_cluster_f64(mine, rank);
+    }
+  }
   __device__ float2 ld2(const float2* mine, unsigned rank) const {
     if constexpr (COOP) {
       const float* p = at(reinterpret_cast<const float*>(mine), rank);

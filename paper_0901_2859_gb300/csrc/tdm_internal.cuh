@@ -70,6 +70,10 @@ struct tdm_plan_s {
   int coop_grid = 0;
   float* coop_scr = nullptr;
   unsigned* coop_ctr = nullptr;
+  // the same for the plain binary64 solve (tdm_solve.cu)
+  int coop64_grid = 0;
+  double* coop64_scr = nullptr;
+  unsigned* coop64_ctr = nullptr;
   cudaEvent_t last = nullptr; // recorded after each solve
   void* host_stage = nullptr; // staging buffers and streams of tdm_solve_host (created on first use)
   // two levels (n beyond one cluster, tdm_large.cu): segments, their plans, responses, reduced plan
@@ -151,6 +155,9 @@ tdm_status tdm_launch_solve(tdm_plan_s* p, const void* F, int64_t ldF, void* X, 
 tdm_status tdm_launch_backward_sums(tdm_plan_s* p, const void* W, const void* X, int64_t ld,
                                     int64_t N, double* da, double* db, tdm_precision prec,
                                     cudaStream_t s);
+// the cooperative binary64 solve's grid for a plan of M blocks of t rows (0:
+// clusters are as good), and the bytes of its scratch
+int tdm_plain_coop_choice(int M, int t, size_t* scr_bytes);
 void tdm_batched_forget(const tdm_plan_s* p);
 tdm_status tdm_launch_batched(tdm_plan_s* const* ps, int count, const void* const* F,
                               const int64_t* ldF, void* const* X, const int64_t* ldX,

@@ -61,6 +61,8 @@ struct SolveArgs {
   int* err;
   int n, M, m, C, ntiles;
   int box_rows;   // TMA box height (divides m * t)
+  double* scr;    // cooperative binary64 solve: every CTA's partials [2 parity][2 dir][R]
+  unsigned* ctr;  // cooperative binary64 solve: the groups' barrier counters (zero at launch)
 };
 
 struct Smem {
@@ -224,13 +226,17 @@ __device__ inline void setup_ratios(const SolveArgs& a, const Smem& s, unsigned 
 }
 
 // A4 up to the incoming partials: LR/LL recurrences, exchange, folds.
-template <typename T, int R>
-__device__ __forceinline__ void separator_partials(const SolveArgs& a, const Smem& s, unsigned c, int parity) {
+// pe: the tile's peers (barrier() and ldd(mine, rank): the cluster, or a group
+// of a cooperative launch); xbase: where this CTA publishes its partials
+// (shared memory, or its scratch block in global memory)
+template <typename T, int R, class PE>
+__device__ __forceinline__ void separator_partials(const SolveArgs& a, const Smem& s, unsigned c, int parity, PE& pe,
+                                                   double* xbase) {
   const int m = a.m;
   const int tid = threadIdx.x;
   const double* betaR = s.betaR;
   const double* betaL = s.betaL;
-  double* xch = s.xch + parity * 2 * R;
+  double* xch = xbase + parity * 2 * R;
   if (tid < R) {                       // SR, left to right
     const int r = tid;
     double lr = 0.0;
@@ -252,7 +258,7 @@ __device__ __forceinline__ void separator_partials(const SolveArgs& a, const Sme
     }
     xch[R + r] = ll;
   }
-  cluster_barrier();
+  pe.barrier();
   // fold the partials of the CTAs to the left (SR) and to the right (SL);
   // remote loads are issued four at a time so that their latencies overlap
   if (tid < R) {
@@ -261,7 +267,7 @@ __device__ __forceinline__ void separator_partials(const SolveArgs& a, const Sme
     for (int c0 = 0; c0 < (int)c; c0 += 4) {
       double v[4];
 #pragma unroll
-      for (int k = 0; k < 4; k++) v[k] = (c0 + k < (int)c) ? ld_cluster_f64(xch + r, (unsigned)(c0 + k)) : 0.0;
+      for (int k = 0; k < 4; k++) v[k] = (c0 + k < (int)c) ? pe.ldd(xch + r, (unsigned)(c0 + k)) : 0.0;
 #pragma unroll
       for (int k = 0; k < 4; k++)
         if (c0 + k < (int)c) in = fma(s.piRtot[c0 + k], in, v[k]);
@@ -274,7 +280,7 @@ __device__ __forceinline__ void separator_partials(const SolveArgs& a, const Sme
     for (int c0 = a.C - 1; c0 > (int)c; c0 -= 4) {
       double v[4];
 #pragma unroll
-      for (int k = 0; k < 4; k++) v[k] = (c0 - k > (int)c) ? ld_cluster_f64(xch + R + r, (unsigned)(c0 - k)) : 0.0;
+      for (int k = 0; k < 4; k++) v[k] = (c0 - k > (int)c) ? pe.ldd(xch + R + r, (unsigned)(c0 - k)) : 0.0;
 #pragma unroll
       for (int k = 0; k < 4; k++)
         if (c0 - k > (int)c) in = fma(s.piLtot[c0 - k], in, v[k]);

@@ -424,6 +424,7 @@ static void tdm_free_plan(tdm_plan_s* p) {
   cudaFree(p->coef64); cudaFree(p->coef32); cudaFree(p->res32); cudaFree(p->rtab);
   cudaFree(p->rR); cudaFree(p->rL); cudaFree(p->a64); cudaFree(p->b64); cudaFree(p->tr);
   cudaFree(p->piv); cudaFree(p->stat); cudaFree(p->dev_err); cudaFree(p->coop_scr); cudaFree(p->coop_ctr);
+  cudaFree(p->coop64_scr); cudaFree(p->coop64_ctr);
   if (p->last) cudaEventDestroy(p->last);
   tdm_host_stage_free(p->host_stage);
   if (p->nseg > 0) tdm_free_large(p);
@@ -571,6 +572,13 @@ static tdm_status prepare_plan(const double* a, const double* b, const double* s
              cudaMalloc(&p->coop_ctr, sizeof(unsigned) * 32 * (grid / sh.C)) == cudaSuccess;
         p->coop_grid = grid;
       }
+    }
+    size_t scr64 = 0;
+    const int grid64 = ok ? tdm_plain_coop_choice(p->M, t, &scr64) : 0;
+    if (grid64 > 0) {
+      ok = cudaMalloc(&p->coop64_scr, scr64) == cudaSuccess &&
+           cudaMalloc(&p->coop64_ctr, sizeof(unsigned) * 32 * (size_t)grid64) == cudaSuccess;
+      p->coop64_grid = grid64;
     }
   }
   if (!ok) {

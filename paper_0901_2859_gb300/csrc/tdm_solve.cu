@@ -39,6 +39,7 @@
 
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -81,7 +82,10 @@ bool tdm_encode_tma_2d(CUtensorMap* out, const void* base, bool fp64, uint64_t c
 namespace {
 using namespace tdmk;
 
-template <typename T, int R, int TT, int MAXT, bool TMA>
+// COOP (binary64 only): a cooperative launch without clusters; groups of a.C
+// consecutive CTAs exchange their partials through a.scr and a counter per
+// group (Link), where clusters of a.C CTAs would leave many SMs idle.
+template <typename T, int R, int TT, int MAXT, bool TMA, bool COOP = false>
 __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const __grid_constant__ CUtensorMap tmF, const SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
@@ -96,7 +100,8 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
   const Smem s = carve(a4, a.m, R, (int)sizeof(T));
   constexpr int MM = MAXT / R;
   const IfaceDF<R, MM, false> f{a4};
-  const unsigned c = cluster_rank();
+  static_assert(!COOP || sizeof(T) == 8, "the cooperative form is the binary64 solve's");
+  const unsigned c = COOP ? blockIdx.x % a.C : cluster_rank();
   const int tid = threadIdx.x;
   const int r = tid % R;
   const int bl = tid / R;
@@ -138,6 +143,17 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
 
   const int cluster_id = blockIdx.x / a.C;
   const int nclusters = gridDim.x / a.C;
+  Link<COOP> lk;
+  double* xbase = nullptr;
+  if constexpr (sizeof(T) == 8) xbase = COOP ? a.scr + (size_t)blockIdx.x * 4 * R : s.xch;
+  if constexpr (COOP) {
+    lk.me = blockIdx.x;
+    lk.first = (unsigned)(cluster_id * a.C);
+    lk.stride = 8 * R;   // floats: 4R doubles per CTA
+    lk.g = (unsigned)a.C;
+    lk.ctr = a.ctr + 32 * cluster_id;
+    lk.err = a.err;
+  }
   const uint32_t tile_bytes = (uint32_t)rows_cta * R * sizeof(T);
   const int nbox = rows_cta / a.box_rows;
   auto issue = [&](int tile) {
@@ -187,7 +203,7 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
         s.betaL[bl * R + r] = bL;
       }
       __syncthreads();
-      separator_partials<T, R>(a, s, c, parity);
+      separator_partials<T, R>(a, s, c, parity, lk, xbase);
       if (blk_ok) {
         if (b >= 1) xL = separator_value<T, R>(s, bl, r);
         if (b + 1 <= a.M - 1) xR = separator_value<T, R>(s, bl + 1, r);
@@ -223,8 +239,9 @@ __global__ void __launch_bounds__(MAXT, (sizeof(T) == 4 ? 2 : 1)) k_solve(const 
     else backward_store<T, TT, false>(v, cfb, nrows, xL, xR, Xp, a.ldX, col_ok);
     parity ^= 1;
   }
-  // no CTA may leave while a peer can still read its shared memory
-  cluster_barrier();
+  // no CTA may leave while a peer can still read its shared memory (the
+  // cooperative form's scratch stays readable)
+  if constexpr (!COOP) cluster_barrier();
 }
 
 // ---------------------------------------------------------------------------
@@ -302,6 +319,79 @@ tdm_status launch_t(const CUtensorMap& map, const SolveArgs& args, const Cfg& cf
   return TDM_OK;
 }
 
+// The cooperative binary64 solve: CTAs per SM of its kernel, and the launch
+// (whole groups of cfg.C CTAs, at most the plan's scratch; the groups'
+// counters are zeroed on the stream first).
+template <int R, int TT, bool TMA>
+int coop_blocks(const Cfg& cfg) {
+  auto kern = k_solve<double, R, TT, 512, TMA, true>;
+  int dev = 0, sms = 0, nb = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.threads, cfg.smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return nb * sms;
+}
+template <int R, int TT, bool TMA>
+tdm_status launch_coop_t(const CUtensorMap& map, const SolveArgs& args, const Cfg& cfg, int max_grid, cudaStream_t s) {
+  auto kern = k_solve<double, R, TT, 512, TMA, true>;
+  const int blocks = std::min(coop_blocks<R, TT, TMA>(cfg), max_grid);
+  const int groups = std::min(blocks / cfg.C, args.ntiles);
+  if (groups < 1) return TDM_ERR_NOT_IMPLEMENTED;
+  TDM_CUDA_TRY(cudaMemsetAsync(args.ctr, 0, sizeof(unsigned) * 32 * groups, s));
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  lc.gridDim = dim3(groups * cfg.C);
+  lc.blockDim = dim3(cfg.threads);
+  lc.dynamicSmemBytes = cfg.smem;
+  lc.stream = s;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  TDM_CUDA_TRY(cudaLaunchKernelEx(&lc, kern, map, args));
+  return TDM_OK;
+}
+template <int TT>
+tdm_status dispatch_coop(const CUtensorMap& map, const SolveArgs& args, const Cfg& cfg, int max_grid, cudaStream_t s) {
+  switch (cfg.R * 2 + (cfg.tma ? 1 : 0)) {
+    case 8 * 2 + 1: return launch_coop_t<8, TT, true>(map, args, cfg, max_grid, s);
+    case 16 * 2 + 1: return launch_coop_t<16, TT, true>(map, args, cfg, max_grid, s);
+    case 8 * 2: return launch_coop_t<8, TT, false>(map, args, cfg, max_grid, s);
+    case 16 * 2: return launch_coop_t<16, TT, false>(map, args, cfg, max_grid, s);
+  }
+  return TDM_ERR_NOT_IMPLEMENTED;
+}
+// CTAs that clusters of the cluster form (cfg.C CTAs each) hold at once
+template <int R, int TT, bool TMA>
+int cluster_slots(const Cfg& cfg) {
+  auto kern = k_solve<double, R, TT, 512, TMA, false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem) != cudaSuccess ||
+      (cfg.C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cfg.C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.blockDim = dim3(cfg.threads);
+  lc.dynamicSmemBytes = cfg.smem;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  lc.gridDim = dim3(cfg.C);
+  int maxc = 0;
+  if (cudaOccupancyMaxActiveClusters(&maxc, (void*)kern, &lc) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return maxc * cfg.C;
+}
+
 template <typename T, int TT, int MAXT>
 tdm_status dispatch(const CUtensorMap& map, const SolveArgs& args, const Cfg& cfg, cudaStream_t s) {
   if (cfg.tma) {
@@ -320,7 +410,38 @@ tdm_status dispatch(const CUtensorMap& map, const SolveArgs& args, const Cfg& cf
   return TDM_ERR_NOT_IMPLEMENTED;
 }
 
+// shared memory of a configuration; the binary32 solve keeps its A4 arrays in
+// the pair layout, sized for 512 / R blocks
+size_t cfg_smem(const Cfg& cfg, int t, bool fp64, bool tma) {
+  const int tsize = fp64 ? 8 : 4;
+  return fp64 ? smem_bytes(cfg.m, t, cfg.R, tsize, tma)
+              : 128 + fbuf_bytes(cfg.m, t, cfg.R, tsize, tma) + coef_bytes(cfg.m, t, tsize) +
+                    iface_offsets(cfg.R, 512 / cfg.R, false).bytes;
+}
+
 }  // namespace
+
+// The cooperative binary64 solve for a plan of M blocks of t rows: the grid
+// (whole groups) when it holds at least 1.2 times the CTAs that clusters of
+// the same width can, else 0; *scr_bytes receives its scratch.
+int tdm_plain_coop_choice(int M, int t, size_t* scr_bytes) {
+  Cfg cfg;
+  if (!choose_cfg(M, t, true, cfg) || cfg.C < 2) return 0;
+  cfg.tma = true;
+  cfg.smem = cfg_smem(cfg, t, true, true);
+  if (cfg.smem > 227 * 1024) return 0;
+  int blocks = 0, slots = 0;
+  switch (cfg.R * 100 + t) {
+    case 8 * 100 + 16: blocks = coop_blocks<8, 16, true>(cfg); slots = cluster_slots<8, 16, true>(cfg); break;
+    case 16 * 100 + 16: blocks = coop_blocks<16, 16, true>(cfg); slots = cluster_slots<16, 16, true>(cfg); break;
+    case 8 * 100 + 32: blocks = coop_blocks<8, 32, true>(cfg); slots = cluster_slots<8, 32, true>(cfg); break;
+    case 16 * 100 + 32: blocks = coop_blocks<16, 32, true>(cfg); slots = cluster_slots<16, 32, true>(cfg); break;
+  }
+  const int grid = blocks / cfg.C * cfg.C;
+  if (grid < cfg.C || (double)grid < 1.2 * (double)slots) return 0;
+  *scr_bytes = sizeof(double) * (size_t)grid * 4 * cfg.R;
+  return grid;
+}
 
 tdm_status tdm_launch_plain(tdm_plan_s* p, const void* F, int64_t ldF, void* X, int64_t ldX,
                             int64_t N, bool fp64, cudaStream_t s) {
@@ -331,16 +452,10 @@ tdm_status tdm_launch_plain(tdm_plan_s* p, const void* F, int64_t ldF, void* X, 
   memset(&map, 0, sizeof(map));
   cfg.tma = tdm_encode_tma_2d(&map, F, fp64, (uint64_t)N, (uint64_t)p->n, (uint64_t)ldF * tsize,
                               (uint32_t)cfg.R, (uint32_t)cfg.box_rows);
-  // the binary32 solve keeps its A4 arrays in the pair layout, sized for 512 / R blocks
-  auto bytes = [&](bool tma) {
-    return fp64 ? smem_bytes(cfg.m, p->t, cfg.R, tsize, tma)
-                : 128 + fbuf_bytes(cfg.m, p->t, cfg.R, tsize, tma) + coef_bytes(cfg.m, p->t, tsize) +
-                      iface_offsets(cfg.R, 512 / cfg.R, false).bytes;
-  };
-  cfg.smem = bytes(cfg.tma);
+  cfg.smem = cfg_smem(cfg, p->t, fp64, cfg.tma);
   if (cfg.smem > 227 * 1024) {   // fall back to direct loads when the staging buffer does not fit
     cfg.tma = false;
-    cfg.smem = bytes(false);
+    cfg.smem = cfg_smem(cfg, p->t, fp64, false);
   }
   SolveArgs args;
   args.F = F; args.X = X; args.ldF = ldF; args.ldX = ldX; args.N = N;
@@ -349,6 +464,12 @@ tdm_status tdm_launch_plain(tdm_plan_s* p, const void* F, int64_t ldF, void* X, 
   args.n = (int)p->n; args.M = p->M; args.m = cfg.m; args.C = cfg.C;
   args.ntiles = (int)((N + cfg.R - 1) / cfg.R);
   args.box_rows = cfg.box_rows;
+  args.scr = p->coop64_scr;
+  args.ctr = p->coop64_ctr;
+  if (fp64 && p->coop64_grid > 0) {   // the cooperative form (chosen at prepare)
+    if (p->t == 16) return dispatch_coop<16>(map, args, cfg, p->coop64_grid, s);
+    return dispatch_coop<32>(map, args, cfg, p->coop64_grid, s);
+  }
   if (fp64) {
     if (p->t == 16) return dispatch<double, 16, 512>(map, args, cfg, s);
     return dispatch<double, 32, 512>(map, args, cfg, s);

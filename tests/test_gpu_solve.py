@@ -209,3 +209,41 @@ def test_largest_supported_size_and_the_next(tdm, dev, oracle, precision, n_max)
     X2 = plan2.solve(F2, precision).double().cpu().numpy()
     assert relerr(X2, oracle.solve_hi(s2.a, s2.b, F2.double().cpu().numpy())) <= (1e-11 if precision == "fp64" else 2e-5)
     plan2.close()
+
+
+def test_cooperative_binary64_solve(tdm, dev, oracle):
+    """n = 16384: the binary64 solve's tiles need 16 CTAs, whose clusters leave
+    a quarter of the SMs idle, so it runs as a cooperative launch whose CTA
+    groups exchange their partials through global memory.  Two solves in a row
+    and a CUDA-graph replay give the same result bit for bit, the result meets
+    the binary64 gate against the oracle, and a general plan of the same matrix
+    (solved with clusters) agrees with it."""
+    from paper_0901_2859_gb300 import workloads
+    s = workloads.precision(seed=4, n=16384, N=203, s=1e-2, dtype=np.float64)
+    plan = tdm.prepare(s.a, s.b, device=dev)
+    F = torch.from_numpy(s.F).to(dev)
+    X1 = plan.solve(F, "fp64")
+    X2 = plan.solve(F, "fp64")
+    torch.cuda.synchronize()
+    assert torch.equal(X1, X2)
+    ref = oracle.solve_hi(s.a, s.b, s.F.astype(np.float64))
+    assert relerr(X1.cpu().numpy(), ref) <= 1e-11
+    gen = tdm.prepare_general(s.a, s.b, s.a, device=dev)
+    Xg = gen.solve(F, "fp64")
+    torch.cuda.synchronize()
+    assert relerr(Xg.cpu().numpy(), X1.cpu().numpy()) <= 1e-12
+    out = torch.empty_like(X1)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        plan.solve(F, "fp64", out=out)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        plan.solve(F, "fp64", out=out)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, X1)
+    assert plan.info()["device_error"] == 0
+    plan.close()
+    gen.close()
