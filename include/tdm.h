@@ -331,6 +331,15 @@ tdm_status tdm_algorithm2_status(const void* work, int64_t P, int64_t n, int64_t
  * Synchronizes the stream. */
 tdm_status tdm_selftest_wait_timeout(int64_t limit_cycles, void* stream);
 
+/* tdm_selftest_group_timeout -- the same check for the group barrier of the
+ * cooperative launches (no counterpart in the paper): in a cooperative grid
+ * of two CTAs forming one group, CTA 1 never arrives; CTA 0 arrives, polls the
+ * group's counter `limit_polls` times (1 .. 2^24), gives up, records device
+ * error 3 and exits; the context stays usable.  Returns TDM_ERR_TIMEOUT when
+ * the wait gave up as it must, TDM_OK if it did not, TDM_ERR_INVALID_ARG for a
+ * limit out of range.  Synchronizes the stream. */
+tdm_status tdm_selftest_group_timeout(int64_t limit_polls, void* stream);
+
 /* tdm_get_info -- plan properties and the device status of the last solve
  * (synchronizes with it). */
 tdm_status tdm_get_info(tdm_handle h, tdm_info* info);

@@ -7,6 +7,7 @@
 
 #include "tdm_internal.cuh"
 #include "tdm_tma.cuh"
+#include "tdm_iface_df.cuh"
 
 tdm_status tdm_launch_plain(tdm_plan_s* p, const void* F, int64_t ldF, void* X, int64_t ldX,
                             int64_t N, bool fp64, cudaStream_t s);
@@ -164,6 +165,47 @@ __global__ void k_wait_selftest(int* err, long long limit) {
 }
 
 }  // namespace
+
+// The group barrier of the cooperative launches with a member that never
+// arrives: CTA 1 of a group of two returns at once, CTA 0 arrives and waits,
+// gives up after `limit` polls and records kDevErrGroupTimeout.
+__global__ void k_group_selftest(unsigned* ctr, int* err, int limit) {
+  if (blockIdx.x != 0) return;
+  tdmk::Link<true> lk;
+  lk.me = 0;
+  lk.first = 0;
+  lk.stride = 0;
+  lk.g = 2;
+  lk.ctr = ctr;
+  lk.err = err;
+  lk.spin_limit = limit;
+  lk.arrive();
+  lk.wait();
+}
+
+extern "C" tdm_status tdm_selftest_group_timeout(int64_t limit_polls, void* stream) {
+  if (limit_polls < 1 || limit_polls > (int64_t(1) << 24)) return TDM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  (void)cudaGetLastError();
+  unsigned* d = nullptr;   // [0]: the counter, [32]: the error word
+  TDM_CUDA_TRY(cudaMalloc(&d, 64 * sizeof(unsigned)));
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, 64 * sizeof(unsigned), s);
+  if (e == cudaSuccess) {
+    int* err = reinterpret_cast<int*>(d + 32);
+    int limit = (int)limit_polls;
+    void* args[] = {&d, &err, &limit};
+    e = cudaLaunchCooperativeKernel((void*)k_group_selftest, dim3(2), dim3(64), args, 0, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d + 32, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TDM_ERR_CUDA;
+  }
+  return h == kDevErrGroupTimeout ? TDM_ERR_TIMEOUT : TDM_OK;
+}
 
 extern "C" tdm_status tdm_selftest_wait_timeout(int64_t limit_cycles, void* stream) {
   if (limit_cycles < 1 || limit_cycles > (int64_t(1) << 31)) return TDM_ERR_INVALID_ARG;

@@ -411,6 +411,7 @@ struct Link {
   int* err = nullptr;
   unsigned narr = 0;       // this CTA's arrivals so far
   bool broken = false;     // a wait timed out (thread 0)
+  int spin_limit = kGroupSpinLimit;   // polls before a wait gives up
   __device__ const float* at(const float* mine, unsigned rank) const {
     return mine + ((int)(first + rank) - (int)me) * stride;
   }
@@ -467,7 +468,7 @@ struct Link {
           unsigned v;
           asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
           if (v >= target) break;
-          if (it >= kGroupSpinLimit) {
+          if (it >= spin_limit) {
             broken = true;
             atomicExch(err, kDevErrGroupTimeout);
             break;

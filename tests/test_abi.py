@@ -106,3 +106,5 @@ def test_host_solve_validation(lib):
 def test_selftest_limit_validation(lib):
     assert lib.tdm_selftest_wait_timeout(0, None) == 1
     assert lib.tdm_selftest_wait_timeout((1 << 31) + 1, None) == 1
+    assert lib.tdm_selftest_group_timeout(0, None) == 1
+    assert lib.tdm_selftest_group_timeout((1 << 24) + 1, None) == 1

@@ -1,6 +1,7 @@
 """Failure detection without a GPU fault: a bounded device wait that nothing
-completes gives up and reports, and a refinement that cannot converge within
-its cap reports device error 2; the context stays usable after both."""
+completes (an mbarrier, or a group barrier whose member never arrives) gives
+up and reports, and a refinement that cannot converge within its cap reports
+device error 2; the context stays usable after each."""
 import numpy as np
 import pytest
 import torch
@@ -16,6 +17,23 @@ def test_bounded_wait_gives_up_and_reports():
     s = workloads.plain_fp64(seed=0, n=500, N=8)                 # the context still works
     plan = tdm.prepare(s.a, s.b, device="cuda:0")
     X = plan.solve(torch.from_numpy(s.F).cuda(), "fp64")
+    torch.cuda.synchronize()
+    assert torch.isfinite(X).all() and plan.info()["device_error"] == 0
+    plan.close()
+
+
+def test_group_barrier_gives_up_and_reports():
+    """The group barrier of the cooperative launches: a member that never
+    arrives makes the other's bounded wait give up with device error 3
+    (TDM_ERR_TIMEOUT from the self-test); the context then still solves, in
+    the cooperative form too."""
+    import paper_0901_2859_gb300 as tdm
+    from paper_0901_2859_gb300 import _lib, workloads
+    lib = _lib.load()
+    assert lib.tdm_selftest_group_timeout(1 << 12, None) == 6
+    s = workloads.precision(seed=1, n=16384, N=40, s=1e-2)
+    plan = tdm.prepare(s.a, s.b, device="cuda:0")
+    X = plan.solve(torch.from_numpy(s.F).cuda(), "fp32_refined")
     torch.cuda.synchronize()
     assert torch.isfinite(X).all() and plan.info()["device_error"] == 0
     plan.close()
