@@ -34,11 +34,11 @@
  *  - Invalid arguments are rejected on the host before any launch with
  *    TDM_ERR_INVALID_ARG; nothing is enqueued in that case.
  *  - Handles are not thread-safe: one host thread at a time per handle.
- *  - Refined solves of one plan must be ordered on the device (one stream, or
- *    streams ordered by events): where clusters of the plan's width would
- *    leave many CTA slots idle (13 to 16 CTAs), the solve is a cooperative
- *    launch whose CTA groups exchange values through a scratch buffer of the
- *    plan.
+ *  - Refined and binary64 solves of one plan must be ordered on the device
+ *    (one stream, or streams ordered by events): where clusters of the plan's
+ *    width would leave many CTA slots idle (13 to 16 CTAs per tile), the solve
+ *    is a cooperative launch whose CTA groups exchange values through a
+ *    scratch buffer of the plan.
  *  - Solves may be captured into a CUDA graph.  A captured solve is not
  *    tracked by tdm_get_info / tdm_destroy; synchronize the graph's stream
  *    before destroying a plan it uses.  A batched call builds its device work
