@@ -466,6 +466,14 @@ def run_adi(args):
     u = pr.solve(f).double()
     err = float((u - f / lam).abs().max() / (f / lam).abs().max())
     iters = len(pr.omegas)
+    # one half step's right-hand side alone (tdm_adi_rhs), along i and along j (transposed
+    # views): binary64 v and f read, binary32 r written, 20 bytes per element
+    n = N - 1
+    buf = torch.empty((n, (n * nprob + 3) // 4 * 4), dtype=torch.float32, device=dev)
+    om = float(pr.omegas[0])
+    rhs_ms = [_events_time(lambda: pr._rhs(x, y, om, buf), steps, 3, torch)
+              for x, y in ((u, f), (u.transpose(0, 1), f.transpose(0, 1)))]
+    rhs_bytes = n * n * nprob * 20
     pr.close()
     pr32 = PeacemanRachford(N, eps, precision="fp32", device=dev)
     ms32 = _events_time(lambda: pr32.solve(f), steps, max(3, args.warmup), torch)
@@ -482,6 +490,8 @@ def run_adi(args):
                    "mesh": [N, N], "problems": nprob, "iterations": iters, "eps": eps},
         "rel_err_vs_exact_discrete": err,
         "binary32_path": {"ms": ms32, "problems_per_s": nprob / (ms32 * 1e-3), "rel_err_vs_exact_discrete": err32},
+        "rhs_kernel": {"ms_along_i": rhs_ms[0], "ms_along_j": rhs_ms[1], "bytes": rhs_bytes,
+                       "gbs_along_i": rhs_bytes / (rhs_ms[0] * 1e6), "gbs_along_j": rhs_bytes / (rhs_ms[1] * 1e6)},
         "prepare_s_all_parameters": prepare_s,
         "paper_context": "about 30 problems/s on 1024 x 1024 (MBC-100k, best processor count; Table 2)",
     }

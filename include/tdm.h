@@ -322,6 +322,24 @@ tdm_status tdm_algorithm2(const double* G, int64_t ldG, int64_t P, int64_t n, co
 tdm_status tdm_algorithm2_status(const void* work, int64_t P, int64_t n, int64_t N, void* stream,
                                  int* device_error);
 
+/* tdm_adi_rhs -- the right-hand side of one Peaceman-Rachford half step
+ * (Section 4b, eqs. adi_iter, adi_iter2), scaled by h^2, in one pass:
+ *   R[a][b*S + s] = c v[a][b][s] + h2 f[a][b][s] + v[a][b-1][s] + v[a][b+1][s]
+ * (v = 0 beyond b's ends), the series of tdm_solve along a whose columns are
+ * the lines b of the problems s (c = omega h^2 - 2, h2 = h^2).
+ *   v, f   device; element (a, b, s) at a*va + b*vb + s (resp. fa, fb), unit
+ *          stride along s, so transposed views of [a][b][s] arrays are
+ *          accepted; binary64 when in_f64, else binary32.
+ *   R      device, [na][ldR], ldR >= nb*S; binary64 when out_f64, else binary32
+ *          (binary32 in with binary64 out is not offered).  Must not overlap
+ *          v or f.
+ * The sums are formed in binary64.  Asynchronous on `stream`.
+ * Errors: TDM_ERR_INVALID_ARG (negative sizes, null pointers, ldR < nb*S, the
+ * binary32-to-binary64 combination), TDM_ERR_CUDA. */
+tdm_status tdm_adi_rhs(const void* v, int64_t va, int64_t vb, const void* f, int64_t fa, int64_t fb, int64_t na,
+                       int64_t nb, int64_t S, double c, double h2, int in_f64, void* R, int64_t ldR, int out_f64,
+                       void* stream);
+
 /* tdm_selftest_wait_timeout -- a check of the failure path of the solve
  * kernels' bounded waits (no counterpart in the paper): one CTA waits on an
  * mbarrier that nothing arrives at, gives up after `limit_cycles` clock

@@ -16,7 +16,7 @@ STATUS_NAMES = {
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_refined": 2}
 
 # every symbol include/tdm.h declares
-EXPORTS = ("tdm_prepare", "tdm_prepare_general", "tdm_solve", "tdm_solve_host", "tdm_solve_batched", "tdm_solve_batched_noalloc", "tdm_set_batched_strategy", "tdm_selftest_group_timeout",
+EXPORTS = ("tdm_prepare", "tdm_prepare_general", "tdm_solve", "tdm_solve_host", "tdm_solve_batched", "tdm_solve_batched_noalloc", "tdm_set_batched_strategy", "tdm_selftest_group_timeout", "tdm_adi_rhs",
            "tdm_solve_backward", "tdm_selftest_wait_timeout", "tdm_get_info", "tdm_destroy",
            "tdm_status_string", "tdm_algorithm2_workspace", "tdm_algorithm2", "tdm_algorithm2_status")
 NOALLOC_MAX_TILES = 4096   # TDM_NOALLOC_MAX_TILES
@@ -76,6 +76,8 @@ def load(build_if_missing: bool = True):
         lib.tdm_get_info.argtypes = [vp, ctypes.POINTER(TDMInfo)]
         lib.tdm_selftest_wait_timeout.argtypes = [i64, vp]
         lib.tdm_selftest_group_timeout.argtypes = [i64, vp]
+        lib.tdm_adi_rhs.argtypes = [vp, i64, i64, vp, i64, i64, i64, i64, i64, ctypes.c_double, ctypes.c_double,
+                                    i32, vp, i64, i32, vp]
         lib.tdm_destroy.argtypes = [vp]
         lib.tdm_status_string.argtypes = [i32]
         lib.tdm_algorithm2_workspace.argtypes = [i64, i64, i64]

@@ -28,19 +28,21 @@ Precision: ``"fp32"`` keeps u in binary32 and solves in binary32. It is the
 fastest, but the binary32 solves of the small-omega systems (condition up to
 about 4 / (pi h)^2) leave an error of order 1e-5 at N = 256. ``"fp32_refined"``
 keeps u in binary64 and solves binary32 right-hand sides to binary64 results.
-``"fp64"`` is binary64 throughout.  The half steps'
-right-hand sides (a three-point difference and a transpose) are PyTorch
-element-wise operations; the tridiagonal series go through the library's
-dichotomy solve.
+``"fp64"`` is binary64 throughout.  The half steps' right-hand sides (a
+three-point difference along the lines, and a transpose every second half
+step) are formed in one pass by the library's ``tdm_adi_rhs`` kernel; the
+tridiagonal series go through its dichotomy solve.
 """
 from __future__ import annotations
 
+import ctypes
 import math
 
 import numpy as np
 import torch
 
-from .api import prepare
+from . import _lib
+from .api import _stream_ptr, check, prepare
 
 __all__ = ["PeacemanRachford", "adi_parameters"]
 
@@ -74,16 +76,26 @@ class PeacemanRachford:
             p.close()
         self.plans = []
 
+    def _rhs(self, v: torch.Tensor, f: torch.Tensor, om: float, buf: torch.Tensor) -> None:
+        """buf[a, (b, s)] = h^2 (omega v + Lambda_b v + f) = (omega h^2 - 2) v + h^2 f
+        + the neighbours along b (u = 0 beyond the ends), formed in one pass into the
+        solver's layout and precision by ``tdm_adi_rhs``; v and f may be transposed views."""
+        n, _, S = v.shape
+        h2 = 1.0 / (self.N * self.N)
+        if v.stride(2) != 1 or f.stride(2) != 1:
+            v, f = v.contiguous(), f.contiguous()
+        st = _lib.load().tdm_adi_rhs(
+            ctypes.c_void_p(v.data_ptr()), v.stride(0), v.stride(1), ctypes.c_void_p(f.data_ptr()), f.stride(0),
+            f.stride(1), n, n, S, om * h2 - 2.0, h2, int(v.dtype == torch.float64), ctypes.c_void_p(buf.data_ptr()),
+            buf.stride(0), int(buf.dtype == torch.float64), _stream_ptr(buf.device))
+        check(st, "tdm_adi_rhs")
+
     def _half_step(self, plan, v: torch.Tensor, f: torch.Tensor, om: float, buf: torch.Tensor) -> torch.Tensor:
         """v, f in the layout [a, b, s]: a the axis the systems run along, b the
         lines (their right-hand sides), s the problem.  Returns w, [a, b, s], with
         tridiag(-1, 2 + omega h^2, -1) w = h^2 (omega v + Lambda_b v + f) along a."""
         n, _, S = v.shape
-        h2 = 1.0 / (self.N * self.N)
-        r = torch.add(v * (om * h2 - 2.0), f, alpha=h2)
-        r[:, 1:] += v[:, :-1]               # the second difference along b, u = 0 beyond the ends
-        r[:, :-1] += v[:, 1:]
-        buf[:, :n * S].view(n, n, S).copy_(r)   # row pitch of buf, rows a (rounded for binary32 solves)
+        self._rhs(v, f, om, buf)
         w = torch.empty(buf.shape, dtype=v.dtype, device=buf.device)
         plan.solve(buf[:, :n * S], self.precision, out=w[:, :n * S])
         return w[:, :n * S].view(n, n, S)

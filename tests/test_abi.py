@@ -103,6 +103,20 @@ def test_host_solve_validation(lib):
     assert lib.tdm_solve_host(None, ctypes.c_void_p(0x1000), 4, ctypes.c_void_p(0x9000), 4, 4, 0, 2, None) == 1
 
 
+def test_adi_rhs_validation(lib):
+    # rejected (or, when empty, accepted) before any CUDA call
+    vp, fake, d = ctypes.c_void_p, ctypes.c_void_p(0x10000), ctypes.c_double
+    def call(v, f, R, na, nb, S, ldR, in64, out64):
+        return lib.tdm_adi_rhs(v, nb * S, S, f, nb * S, S, na, nb, S, d(-2.0), d(1.0), in64, R, ldR, out64, None)
+    assert call(fake, fake, fake, -1, 4, 2, 8, 1, 1) == 1
+    assert call(fake, fake, fake, 4, 4, -2, 8, 1, 1) == 1
+    assert call(fake, fake, fake, 4, 4, 2, 8, 0, 1) == 1        # binary32 in, binary64 out
+    assert call(fake, fake, fake, 0, 4, 2, 8, 1, 1) == 0        # empty
+    assert call(None, fake, fake, 4, 4, 2, 8, 1, 1) == 1
+    assert call(fake, fake, None, 4, 4, 2, 8, 0, 0) == 1
+    assert call(fake, fake, fake, 4, 4, 2, 7, 1, 0) == 1        # ldR < nb * S
+
+
 def test_selftest_limit_validation(lib):
     assert lib.tdm_selftest_wait_timeout(0, None) == 1
     assert lib.tdm_selftest_wait_timeout((1 << 31) + 1, None) == 1

@@ -1,7 +1,9 @@
 """Host logic of the alternating-direction solver (Section 4b) on CPU: the
-half steps' right-hand sides, layouts and transposes, with the library's solve
-replaced by the oracle's sweep (a fake plan), against the oracle's iteration;
-and the parameters against the oracle's."""
+half steps' layouts, transposes and precisions, with the library's solve
+replaced by the oracle's sweep (a fake plan) and its right-hand-side kernel by
+the three-point difference written out here, against the oracle's iteration;
+and the parameters against the oracle's.  The kernel itself is compared with
+that difference on the GPU."""
 import numpy as np
 import pytest
 import torch
@@ -17,6 +19,19 @@ class _FakePlan:
         return out
 
 
+def _fake_rhs(pr):
+    """The half step's right-hand side h^2 (omega v + Lambda_b v + f), u = 0 beyond
+    the ends of b, into buf[a, (b, s)] in buf's precision."""
+    def rhs(v, f, om, buf):
+        n, _, S = v.shape
+        h2 = 1.0 / (pr.N * pr.N)
+        r = v.double().clone() * (om * h2 - 2.0) + h2 * f.double()
+        r[:, 1:] += v[:, :-1].double()
+        r[:, :-1] += v[:, 1:].double()
+        buf[:, :n * S].view(n, n, S).copy_(r)
+    return rhs
+
+
 def _fake_solver(N, eps, precision):
     from paper_0901_2859_gb300.adi import PeacemanRachford, adi_parameters
     pr = PeacemanRachford.__new__(PeacemanRachford)
@@ -24,6 +39,7 @@ def _fake_solver(N, eps, precision):
     pr.omegas = adi_parameters(N, eps)
     n, h = N - 1, 1.0 / N
     pr.plans = [_FakePlan(-np.ones(n - 1), np.full(n, 2.0 + om * h * h)) for om in pr.omegas]
+    pr._rhs = _fake_rhs(pr)
     return pr
 
 
