@@ -333,9 +333,15 @@ tdm_status tdm_algorithm2_status(const void* work, int64_t P, int64_t n, int64_t
  *   R      device, [na][ldR], ldR >= nb*S; binary64 when out_f64, else binary32
  *          (binary32 in with binary64 out is not offered).  Must not overlap
  *          v or f.
- * The sums are formed in binary64.  Asynchronous on `stream`.
- * Errors: TDM_ERR_INVALID_ARG (negative sizes, null pointers, ldR < nb*S, the
- * binary32-to-binary64 combination), TDM_ERR_CUDA. */
+ * Arithmetic: binary64 results are summed in binary64; binary64 inputs with
+ * binary32 results are summed in pairs of binary32 numbers (about 2^-47 of
+ * the terms, then one rounding), falling back to binary64 for elements
+ * outside the pairs' range (0 < |x| < 2^-74, |x| >= 2^128, non-finite) or
+ * when c or h2 is nonzero and outside [2^-60, 2^60]; binary32 inputs are summed in
+ * binary32.  Asynchronous on `stream`.
+ * Errors: TDM_ERR_INVALID_ARG (negative sizes, null pointers, ldR < nb*S,
+ * nb*S above 2^31 - 1, the binary32-to-binary64 combination), TDM_ERR_CUDA.
+ * Empty sizes return TDM_OK without a launch. */
 tdm_status tdm_adi_rhs(const void* v, int64_t va, int64_t vb, const void* f, int64_t fa, int64_t fb, int64_t na,
                        int64_t nb, int64_t S, double c, double h2, int in_f64, void* R, int64_t ldR, int out_f64,
                        void* stream);
