@@ -8,10 +8,12 @@
 // with v = 0 beyond b's ends.  The solver takes it as the rows a of a series
 // whose columns are (b, s).  The second half step of an iteration runs along
 // the other axis, so v and f arrive as transposed views: element (a, b, s) at
-// a * sa + b * sb + s.  Both layouts keep s contiguous, so a CTA's run of
-// columns j = b * S + s of one row a reads runs of S contiguous elements and
-// the pass needs no transpose buffer: it reads v and f once (the neighbours
-// along b come from cache) and writes r once, in the solver's precision.
+// a * sa + b * sb + s.  Both layouts keep s contiguous.  A thread takes one
+// (a, s) and kRhsB consecutive lines b, holding v of lines b0 - 1 .. b0 + kRhsB
+// in registers (the window each line's neighbours come from); the lanes of a
+// warp take consecutive s, so every load and store of a line is one contiguous
+// run.  The pass reads v and f once (the window's two extra lines come from
+// cache) and writes r once, in the solver's precision, with no transpose buffer.
 //
 // Arithmetic.  For smooth v the sum cancels: |r| is about omega h^2 |v|, far
 // below |v|, and the solve multiplies an error in r by up to 1 / (omega h^2).
@@ -21,9 +23,10 @@
 // their encodings (truncated high part, the remaining 29 bits rounded into the
 // low part: 2^-47 relative), and the sum is formed in pair arithmetic
 // (Dekker's exact sum and product, Knuth's two-sum) on the binary32 pipes.
-// Inputs outside the pairs' range (|x| below 2^-74 or at 2^128 and above, but
-// not 0, and non-finite values) take the binary64 path for that element, and
-// every element does when c or h^2 lies outside [2^-60, 2^60].  A
+// Each binary64 value is split once.  A thread whose window holds a value
+// outside the pairs' range (|x| below 2^-74 or at 2^128 and above, but not 0,
+// and non-finite values) forms its lines in binary64, and every thread does
+// when c or h^2 lies outside [2^-60, 2^60].  A
 // binary64 result is formed in binary64; binary32 inputs are summed in binary32,
 // the precision their state already has.
 #include <stdint.h>
@@ -33,7 +36,7 @@
 namespace {
 
 constexpr int kRhsThreads = 256;
-constexpr int kRhsPer = 4;   // elements per thread
+constexpr int kRhsB = 4;   // lines b per thread: 4 with 64 registers (4 CTAs per SM) measured fastest
 
 struct Pair {
   float h, l;
@@ -78,51 +81,57 @@ __device__ __forceinline__ Pair pair_mul(Pair a, Pair b) {
   return Pair{h, __fsub_rn(e, __fsub_rn(h, p))};
 }
 
-template <typename TO>
-__device__ __forceinline__ TO rhs64(double v, double f, double vl, double vr, double c, double h2, Pair cp, Pair hp,
-                                    bool ok) {
-  if constexpr (sizeof(TO) == 8) return c * v + h2 * f + vl + vr;
-  const Pair pv = split64(v, ok), pf = split64(f, ok), pl = split64(vl, ok), pr = split64(vr, ok);
-  if (!ok) return (TO)(c * v + h2 * f + vl + vr);
-  const Pair r = pair_add(pair_add(pair_add(pl, pr), pair_mul(cp, pv)), pair_mul(hp, pf));
-  return (TO)__fadd_rn(r.h, r.l);
-}
-
-// grid: x over runs of kRhsThreads * kRhsPer columns j = b * S + s of a row, y over rows a
+// grid: x over (chunk of kRhsB lines, s) of a row, y over rows a
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(kRhsThreads) k_adi_rhs(const TI* __restrict__ v, int64_t va, int64_t vb,
+__global__ void __launch_bounds__(kRhsThreads, 4) k_adi_rhs(const TI* __restrict__ v, int64_t va, int64_t vb,
                                                          const TI* __restrict__ f, int64_t fa, int64_t fb,
-                                                         int64_t na, unsigned nb, unsigned S, double c, double h2,
-                                                         Pair cp, Pair hp, bool pairs, TO* __restrict__ r,
-                                                         int64_t ldr) {
-  const unsigned ncols = nb * S;
+                                                         int64_t na, unsigned nb, unsigned S, unsigned nchunks,
+                                                         double c, double h2, Pair cp, Pair hp, bool pairs,
+                                                         TO* __restrict__ r, int64_t ldr) {
+  const unsigned t = blockIdx.x * kRhsThreads + threadIdx.x;
+  if (t >= S * nchunks) return;   // no barrier below
+  const unsigned chunk = t / S, s = t - chunk * S;
+  const int64_t b0 = (int64_t)chunk * kRhsB;
   for (int64_t a = blockIdx.y; a < na; a += gridDim.y) {
-    const TI* va_ = v + a * va;
-    const TI* fa_ = f + a * fa;
-    TO* ra = r + a * ldr;
-    TI x[kRhsPer], y[kRhsPer], xl[kRhsPer], xr[kRhsPer];
-    unsigned jj[kRhsPer];
+    const TI* vp = v + a * va + s;
+    const TI* fp = f + a * fa + s;
+    TO* rp = r + a * ldr + s;
+    auto ldv = [&](int k) -> TI {   // v of line b0 + k - 1, 0 beyond the ends
+      const int64_t bb = b0 + k - 1;
+      return (bb >= 0 && bb < (int64_t)nb) ? vp[bb * vb] : TI(0);
+    };
+    auto ldf = [&](int k) -> TI { return b0 + k < (int64_t)nb ? fp[(b0 + k) * fb] : TI(0); };
+    if constexpr (sizeof(TI) == 8 && sizeof(TO) == 4) {
+      // split as loaded (the raw values are not kept: a window that needs the
+      // binary64 path loads them again)
+      bool ok = pairs;
+      Pair pw[kRhsB + 2], pf[kRhsB];
 #pragma unroll
-    for (int k = 0; k < kRhsPer; ++k) {
-      const unsigned j = (blockIdx.x * kRhsPer + k) * kRhsThreads + threadIdx.x;
-      jj[k] = j;
-      x[k] = y[k] = xl[k] = xr[k] = TI(0);
-      if (j < ncols) {
-        const unsigned b = j / S, s = j - b * S;
-        const int64_t ov = (int64_t)b * vb + s;
-        x[k] = va_[ov];
-        y[k] = fa_[(int64_t)b * fb + s];
-        if (b > 0) xl[k] = va_[ov - vb];
-        if (b + 1 < nb) xr[k] = va_[ov + vb];
+      for (int k = 0; k < kRhsB + 2; ++k) pw[k] = split64(ldv(k), ok);
+#pragma unroll
+      for (int k = 0; k < kRhsB; ++k) pf[k] = split64(ldf(k), ok);
+      if (ok) {
+#pragma unroll
+        for (int k = 0; k < kRhsB; ++k) {
+          if (b0 + k >= (int64_t)nb) break;
+          const Pair q = pair_add(pair_add(pair_add(pw[k], pw[k + 2]), pair_mul(cp, pw[k + 1])), pair_mul(hp, pf[k]));
+          rp[(b0 + k) * S] = __fadd_rn(q.h, q.l);
+        }
+        continue;
       }
     }
+    TI w[kRhsB + 2], y[kRhsB];
 #pragma unroll
-    for (int k = 0; k < kRhsPer; ++k) {
-      if (jj[k] >= ncols) continue;
+    for (int k = 0; k < kRhsB + 2; ++k) w[k] = ldv(k);
+#pragma unroll
+    for (int k = 0; k < kRhsB; ++k) y[k] = ldf(k);
+#pragma unroll
+    for (int k = 0; k < kRhsB; ++k) {
+      if (b0 + k >= (int64_t)nb) break;
       if constexpr (sizeof(TI) == 8)
-        ra[jj[k]] = rhs64<TO>(x[k], y[k], xl[k], xr[k], c, h2, cp, hp, pairs);
+        rp[(b0 + k) * S] = (TO)(c * w[k + 1] + h2 * y[k] + w[k] + w[k + 2]);
       else
-        ra[jj[k]] = (TO)((float)c * (float)x[k] + (float)h2 * (float)y[k] + (float)xl[k] + (float)xr[k]);
+        rp[(b0 + k) * S] = (TO)((float)c * w[k + 1] + (float)h2 * y[k] + w[k] + w[k + 2]);
     }
   }
 }
@@ -148,18 +157,18 @@ extern "C" tdm_status tdm_adi_rhs(const void* v, int64_t va, int64_t vb, const v
   if (!v || !f || !R || ldR < nb * S || nb * S > (int64_t)INT32_MAX) return TDM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   (void)cudaGetLastError();
-  const int64_t per_cta = (int64_t)kRhsThreads * kRhsPer;
-  const dim3 grid((unsigned)((nb * S + per_cta - 1) / per_cta), (unsigned)(na < 65535 ? na : 65535));
+  const unsigned nchunks = (unsigned)((nb + kRhsB - 1) / kRhsB);
+  const dim3 grid((unsigned)(((int64_t)nchunks * S + kRhsThreads - 1) / kRhsThreads), (unsigned)(na < 65535 ? na : 65535));
   const Pair cp = host_pair(c), hp = host_pair(h2);
   const bool pairs = pair_range(c) && pair_range(h2);
   if (in_f64 && out_f64)
     k_adi_rhs<double, double><<<grid, kRhsThreads, 0, s>>>(static_cast<const double*>(v), va, vb, static_cast<const double*>(f),
-                                                   fa, fb, na, (unsigned)nb, (unsigned)S, c, h2, cp, hp, pairs, static_cast<double*>(R), ldR);
+                                                   fa, fb, na, (unsigned)nb, (unsigned)S, nchunks, c, h2, cp, hp, pairs, static_cast<double*>(R), ldR);
   else if (in_f64)
     k_adi_rhs<double, float><<<grid, kRhsThreads, 0, s>>>(static_cast<const double*>(v), va, vb, static_cast<const double*>(f),
-                                                  fa, fb, na, (unsigned)nb, (unsigned)S, c, h2, cp, hp, pairs, static_cast<float*>(R), ldR);
+                                                  fa, fb, na, (unsigned)nb, (unsigned)S, nchunks, c, h2, cp, hp, pairs, static_cast<float*>(R), ldR);
   else
     k_adi_rhs<float, float><<<grid, kRhsThreads, 0, s>>>(static_cast<const float*>(v), va, vb, static_cast<const float*>(f),
-                                                 fa, fb, na, (unsigned)nb, (unsigned)S, c, h2, cp, hp, pairs, static_cast<float*>(R), ldR);
+                                                 fa, fb, na, (unsigned)nb, (unsigned)S, nchunks, c, h2, cp, hp, pairs, static_cast<float*>(R), ldR);
   return cudaGetLastError() == cudaSuccess ? TDM_OK : TDM_ERR_CUDA;
 }
