@@ -335,9 +335,10 @@ tdm_status tdm_algorithm2_status(const void* work, int64_t P, int64_t n, int64_t
  *          v or f.
  * Arithmetic: binary64 results are summed in binary64; binary64 inputs with
  * binary32 results are summed in pairs of binary32 numbers (about 2^-47 of
- * the terms, then one rounding), falling back to binary64 for elements
- * outside the pairs' range (0 < |x| < 2^-74, |x| >= 2^128, non-finite) or
- * when c or h2 is nonzero and outside [2^-60, 2^60]; binary32 inputs are summed in
+ * the terms, then one rounding); binary64 arithmetic instead for a run of
+ * four lines b of one (a, s) whose inputs include a value outside the pairs'
+ * range (0 < |x| < 2^-74, |x| >= 2^128, non-finite), and everywhere when c or
+ * h2 is nonzero and outside [2^-60, 2^60]; binary32 inputs are summed in
  * binary32.  Asynchronous on `stream`.
  * Errors: TDM_ERR_INVALID_ARG (negative sizes, null pointers, ldR < nb*S,
  * nb*S above 2^31 - 1, the binary32-to-binary64 combination), TDM_ERR_CUDA.
