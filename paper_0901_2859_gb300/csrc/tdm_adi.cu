@@ -25,10 +25,10 @@
 // (Dekker's exact sum and product, Knuth's two-sum) on the binary32 pipes.
 // Each binary64 value is split once.  A thread whose window holds a value
 // outside the pairs' range (|x| below 2^-74 or at 2^128 and above, but not 0,
-// and non-finite values) forms its lines in binary64, and every thread does
-// when c or h^2 lies outside [2^-60, 2^60].  A
-// binary64 result is formed in binary64; binary32 inputs are summed in binary32,
-// the precision their state already has.
+// and non-finite values) loads them again and forms its lines in binary64, and
+// every thread does when c or h^2 is nonzero and outside [2^-60, 2^60].  A
+// binary64 result is formed in binary64; binary32 inputs are summed in
+// binary32, the precision their state already has.
 #include <stdint.h>
 
 #include "tdm_internal.cuh"
