@@ -82,6 +82,8 @@ class PeacemanRachford:
         solver's layout and precision by ``tdm_adi_rhs``; v and f may be transposed views."""
         n, _, S = v.shape
         h2 = 1.0 / (self.N * self.N)
+        if f.dtype != v.dtype or f.shape != v.shape:
+            raise ValueError("v and f must have one dtype and shape")
         if v.stride(2) != 1 or f.stride(2) != 1:
             v, f = v.contiguous(), f.contiguous()
         st = _lib.load().tdm_adi_rhs(
